@@ -1,0 +1,98 @@
+"""Pins for the oracle's Algorithm 1: closed-form separable spectra, a gauge-
+transformed complex pencil, brute force, Sylvester inertia, residual metrics."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import apply as AP
+from oracle import eigs as E
+from oracle import filter as F
+from paper_1701_08935_gb300 import synth
+
+
+def _closed_form_2d(n, w=0.1):
+    i = np.arange(1, n + 1)
+    kap = 2 - 2 * np.cos(i * math.pi / (n + 1))
+    mu = 2.0 / 3.0 + np.cos(i * math.pi / (n + 1)) / 3.0
+    # lambda_ij = (kappa_i + kappa_j) / (1 + w mu_i), i the x index
+    return np.sort((kap[:, None] + kap[None, :]).ravel() / np.repeat(1 + w * mu, n))
+
+
+def test_dense_eigs_match_closed_form():
+    n = 12
+    A = synth.laplacian((n, n))
+    B = synth.mass_x((n, n))
+    lam, V = E.dense_eigs(A, B)
+    assert np.allclose(lam, _closed_form_2d(n), rtol=1e-12, atol=1e-13)
+    assert np.allclose(V.conj().T @ (B @ V), np.eye(n * n), atol=1e-12)
+
+
+def _interval(lam, p, q):
+    return (lam[p - 1], lam[p], lam[q - 1], lam[q])   # eigenvalues p+1..q are inside
+
+
+@pytest.mark.parametrize("r", [(2, 2), (2, 3)])
+def test_subspace_iteration_recovers_closed_form(r):
+    n = 12
+    A = synth.laplacian((n, n))
+    B = synth.mass_x((n, n))
+    exact = _closed_form_2d(n)
+    # choose an interval with clean gaps around it
+    gaps = _interval(exact, 20, 36)
+    assert gaps[1] - gaps[0] > 1e-3 and gaps[3] - gaps[2] > 1e-3
+    flt = F.ZoloFilter(*gaps, *r)
+    a, b = 0.5 * (gaps[0] + gaps[1]), 0.5 * (gaps[2] + gaps[3])
+    X0 = synth.random_block(n * n, 24, 5, complex_=False)
+    lam, X = E.subspace_iteration(A, B, a, b, X0, lambda Q: AP.apply_exact(A, B, Q, flt), n_iter=4)
+    assert len(lam) == 16
+    assert np.allclose(lam, exact[20:36], rtol=1e-10)
+    assert np.max(E.residuals(A, B, lam, X)) < 1e-10
+    # e_{Lambda,X} divides by max(|a|,|b|) ||B x|| (~4x smaller than ||A||_inf ||x|| here)
+    assert E.relerr(A, B, lam, X, a, b) < 1e-9
+    XtBX = X.conj().T @ (B @ X)
+    assert np.allclose(XtBX, np.eye(len(lam)), atol=1e-10)
+
+
+def test_gauge_phase_keeps_spectrum():
+    """A constant phase e^{i theta} on every x-link of A and B is the gauge transform
+    D = diag(e^{i theta x}) applied to both, so the complex Hermitian pencil
+    (D A D^H, D B D^H) has exactly the real pencil's spectrum."""
+    n = 6
+    dims = (n, n, n)
+    A0 = synth.laplacian(dims)
+    N = n ** 3
+    idx = np.arange(N)
+    x = idx % n
+    D = sp.diags(np.exp(1j * 0.7 * x))
+    A1 = (D @ A0 @ D.conj().T).tocsr()
+    B = synth.mass_trilinear(dims)
+    l0, _ = E.dense_eigs(A0, B)
+    B1 = (D @ B @ D.conj().T).tocsr()
+    assert abs(B1 - B).max() > 0.01           # genuinely complex B
+    l1, _ = E.dense_eigs(A1, B1)
+    assert np.allclose(l0, l1, atol=1e-11)
+    # and the 3D separable closed form (kappa_i + kappa_j + kappa_l)/(mu_i mu_j mu_l)
+    i = np.arange(1, n + 1)
+    kap = 2 - 2 * np.cos(i * math.pi / (n + 1))
+    mu = 2.0 / 3.0 + np.cos(i * math.pi / (n + 1)) / 3.0
+    cf = np.sort(((kap[:, None, None] + kap[None, :, None] + kap[None, None, :])
+                  / (mu[:, None, None] * mu[None, :, None] * mu[None, None, :])).ravel())
+    assert np.allclose(l0, cf, rtol=1e-11)
+
+
+def test_inertia_counts_match_dense():
+    p = synth.pencil_3d_peierls(5, seed=2, wells=4)
+    lam, _ = E.dense_eigs(p.A, p.B)
+    for a, b in [(lam[10] + 1e-6, lam[40] + 1e-6), (-10.0, lam[3] + 1e-6)]:
+        assert E.count_in(p.A, p.B, a, b) == int(np.sum((lam > a) & (lam < b)))
+
+
+def test_residual_metric_flags_a_wrong_pair():
+    p = synth.pencil_2d_real(8, seed=1)
+    lam, V = E.dense_eigs(p.A, p.B)
+    good = E.residuals(p.A, p.B, lam[:5], V[:, :5])
+    assert np.max(good) < 1e-13
+    bad = E.residuals(p.A, p.B, lam[:5] * (1 + 1e-6), V[:, :5])
+    assert np.min(bad) > 1e-8
