@@ -1,0 +1,233 @@
+/*
+ * zolo.h -- C ABI of the GB300 Zolotarev-filter interior eigensolver.
+ *
+ * Problem (Section 1, eq. IGEVP): for a sparse Hermitian-definite pencil (A, B)
+ * (A, B Hermitian, B positive definite) and an interval (a, b), find every
+ * eigenpair A x = lambda B x with a < lambda < b.  The method (Li & Yang,
+ * arXiv:1701.08935) applies the rational filter
+ *      R_ab(x) = ( Z_2r2( Zhat_2r1( T(x); l1 ); l2 ) + 1 ) / 2          (eq. R2)
+ * to a block of vectors inside subspace iteration (Algorithm 1), evaluating it with
+ * the hybrid method of Algorithm 2: r1 factored shifted matrices K_j = A - sigma_j B
+ * give the inner operator G = Zhat(T(B^-1 A)) (eq. solve), and shift-invariant GMRES
+ * over the 2 r2 shifts +-i sqrt(c_2j-1) gives Z(G) (eq. solve2).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status (ZOLO_OK = 0); nothing throws across the
+ *    ABI.  zolo_last_error() gives a thread-local message for the last failure.
+ *  - Matrices enter as host CSR (zolo_csr): 0-based, n x n, full pattern (both
+ *    triangles), column indices sorted inside each row; the library copies what it
+ *    keeps, the caller keeps ownership of its arrays.
+ *  - Vector blocks are DEVICE arrays of complex double (interleaved re, im) laid out
+ *    row-major: entry (i, c) of an n x k block sits at X[i*ld + c], ld >= k (a
+ *    contiguous torch tensor of shape (n, k) has ld = k).  Rows use the caller's
+ *    (original) numbering.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls that return results to the host synchronise that stream.
+ *  - Handles own their device memory until the matching destroy call.
+ *  - Single GPU, the current CUDA device at the time of the call.
+ */
+#ifndef ZOLO_H
+#define ZOLO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define ZOLO_OK        0
+#define ZOLO_EINVAL    1  /* bad argument: shapes, ordering, non-finite, a- >= a+ ... */
+#define ZOLO_ENOTHERM  2  /* A or B not Hermitian within a relative 1e-12 */
+#define ZOLO_ENOMEM    3  /* device or host allocation failed */
+#define ZOLO_ESINGULAR 4  /* zero / non-finite pivot in a front */
+#define ZOLO_ENOCONV   5  /* residuals above tolerance after the allowed iterations */
+#define ZOLO_ETIMEOUT  6  /* a bounded device wait expired */
+#define ZOLO_ECUDA     7  /* a CUDA runtime call failed */
+#define ZOLO_EGAP      8  /* a converged Ritz value lies inside a declared eigengap */
+
+/* ---- value types of CSR arrays ------------------------------------------ */
+#define ZOLO_R64  1       /* double */
+#define ZOLO_C128 2       /* complex double, interleaved (re, im) */
+
+/* ---- arithmetic of the factorisation and solves ------------------------- */
+#define ZOLO_PREC_FP64  0 /* complex128 everywhere */
+#define ZOLO_PREC_MIXED 1 /* complex64 fronts and solves (FP64 diagonal blocks), each
+                             shifted solve refined to FP64 accuracy against the FP64
+                             pencil; Krylov basis, least squares, Gram and Rayleigh-Ritz
+                             stay FP64 */
+
+#define ZOLO_MAX_R 16     /* largest r1, r2 accepted */
+
+typedef struct {
+    int64_t        n;        /* rows = columns */
+    int64_t        nnz;
+    const int64_t *row_ptr;  /* n+1 entries, host */
+    const int32_t *col_idx;  /* nnz entries, host, sorted within each row */
+    const void    *val;      /* nnz values of type `dtype`, host */
+    int32_t        dtype;    /* ZOLO_R64 or ZOLO_C128 */
+    int32_t        reserved;
+} zolo_csr;
+
+/* Filter specification: the eigengaps (a-, a+) around a and (b-, b+) around b
+ * (Section 1, "Contribution"; Algorithm 2 line 1).  a_minus may be -INFINITY (the
+ * lowest slice, as in Section 3.1).  r1 / r2 are the inner (factored) and outer
+ * (GMRES) Zolotarev orders; if either is <= 0 the smallest r = r1 = r2 with
+ * delta0 <= eps is chosen (Remark after Algorithm 2).                       */
+typedef struct {
+    double  a_minus, a_plus, b_minus, b_plus;
+    int32_t r1, r2;
+    double  eps;
+} zolo_filter_spec;
+
+/* Everything Algorithm 2 lines 2-4 compute. */
+typedef struct {
+    double  alpha, beta, gamma;         /* T(x) = gamma (x - alpha)/(x - beta)  (eq. mo) */
+    double  ell1, ell2;                 /* eq. req and l2 = Zhat(l1; l1)              */
+    double  delta1;                     /* error of Z_2r1(.; l1)                       */
+    double  delta0;                     /* max |R_ab - S_ab| on the gap complement (Thm 3) */
+    int32_t r1, r2;
+    double  M_hat;                      /* M of Zhat_2r1 (divided by max Z)            */
+    double  const_hat;                  /* M_hat sum_j a_hat_j gamma/(gamma^2 + c_hat_j) */
+    double  a_hat[ZOLO_MAX_R];          /* Prop. 1 weights of the inner function       */
+    double  c_hat[ZOLO_MAX_R];          /* c_hat_{2j-1}                                */
+    double  sigma_hat[2 * ZOLO_MAX_R];  /* factored poles (re, im), Prop. 2            */
+    double  w_hat[2 * ZOLO_MAX_R];      /* their weights (re, im), M_hat included      */
+    double  M;                          /* M of the outer Z_2r2(.; l2)                 */
+    double  a[ZOLO_MAX_R];              /* outer weights a_j (Cor. 1)                  */
+    double  c[ZOLO_MAX_R];              /* outer c_{2j-1}: shifts are +-i sqrt(c)      */
+} zolo_filter_info;
+
+/* Options.  zolo_opts_default() fills the documented defaults. */
+typedef struct {
+    int32_t  grid[3];      /* grid dims for geometric nested dissection (vertex id
+                              x + nx (y + ny z)); grid[0] <= 0: no geometry, a single
+                              dense front (only for n <= 8192)                  */
+    int32_t  leaf_max;     /* nested-dissection leaf size (default 32)            */
+    int32_t  precision;    /* ZOLO_PREC_FP64 (default) or ZOLO_PREC_MIXED         */
+    int32_t  gmres_m_max;  /* GMRES steps at most (default 40)                    */
+    double   gmres_tol;    /* stop when every shift's least-squares residual is
+                              <= gmres_tol * ||x_c|| for every column (default 1e-12) */
+    int32_t  refine_max;   /* refinement steps per shifted solve, MIXED (default 8) */
+    double   refine_tol;   /* refinement stops at ||b - K x|| <= refine_tol ||b|| (1e-13) */
+    int32_t  n_iter_max;   /* subspace iterations at most (default 4)             */
+    double   tol;          /* eigenpair residual ||Ax - lam Bx||/(||A||_inf ||x||) (1e-10) */
+    double   drop_tol;     /* B-Gram eigenvalues below drop_tol * max are dropped (1e-14) */
+    int32_t  k;            /* subspace dimension; <= 0: ceil(1.5 n_est) + 8        */
+    int32_t  r1, r2;       /* filter orders used by zolo_eigs (default 2, 2)       */
+    double   gap_rel;      /* zolo_eigs without gaps: a- = a - g, b+ = b + g with
+                              g = gap_rel (b - a) (default 1e-2)                  */
+    uint64_t seed;         /* starting block: SplitMix64-seeded normal entries     */
+    int32_t  verbose;      /* 0 silent, 1 stages to stderr                         */
+    int32_t  reserved;
+} zolo_opts;
+
+/* Counters and timings filled by zolo_apply / zolo_eigs (n_solv as Section 3 counts it). */
+typedef struct {
+    int32_t n_iter;            /* subspace iterations run                      */
+    int32_t n_gmres;           /* GMRES steps of the last filter application   */
+    int64_t n_solv;            /* shifted solves: r * n_ss * n_iter * n_gmres   */
+    int32_t n_refine_max;      /* largest refinement count of one solve (MIXED) */
+    int32_t n_found;           /* eigenpairs returned                           */
+    double  gmres_res;         /* worst relative least-squares residual         */
+    double  max_resid;         /* worst eigenpair residual                      */
+    double  relerr;            /* e_{Lambda,X} of eq. relerr                    */
+    double  t_factor_ms, t_apply_ms, t_rr_ms, t_total_ms;
+    double  min_pivot;         /* smallest |pivot| over all fronts and poles    */
+    double  flops_factor;      /* algorithmic flops of one factorisation set    */
+    double  flops_solve;       /* algorithmic flops of one block solve (k = 1)  */
+} zolo_stats;
+
+typedef struct zolo_filter_s   *zolo_filter;
+typedef struct zolo_symbolic_s *zolo_symbolic;
+typedef struct zolo_factor_s   *zolo_factor_h;
+
+typedef struct {
+    int64_t n, nnodes, nlevels;
+    int64_t nnz_factor;        /* entries of L below the diagonal held by fronts     */
+    int64_t front_entries;     /* sum over fronts of nf^2 (dense front storage)      */
+    int64_t update_rows;       /* sum over fronts of the update-row counts           */
+    int32_t max_front, max_pivots;
+    double  flops_lu;          /* real flops of one complex no-pivot LU (all fronts) */
+} zolo_symbolic_info;
+
+/* ---- misc ---------------------------------------------------------------- */
+void        zolo_opts_default(zolo_opts *opts);
+const char *zolo_strerror(int status);
+const char *zolo_last_error(void);              /* thread-local detail message */
+int         zolo_version(void);                 /* 100 * major + minor */
+
+/* ---- filter (host only; Algorithm 2 lines 1-4) -------------------------- */
+/* Build R_ab: Moebius map from eq. req, Zolotarev coefficients (Thm 1), rescaling
+ * (eq. rZ), l2, partial fractions (Prop. 1, Cor. 1) and inner poles/weights (Prop. 2).
+ * EINVAL unless a- < a+ < b- < b+ (a- may be -inf), 1 <= r <= ZOLO_MAX_R.       */
+int  zolo_filter_build(const zolo_filter_spec *spec, zolo_filter *out);
+int  zolo_filter_get_info(zolo_filter f, zolo_filter_info *out);
+/* R_ab(x[i]) for n real points, host arrays. */
+int  zolo_filter_eval(zolo_filter f, int64_t n, const double *x, double *out);
+void zolo_filter_destroy(zolo_filter f);
+
+/* ---- ordering and symbolic analysis (host only, once per pattern) ------- */
+/* Nested dissection of pattern(A) U pattern(B), assembly tree and front row lists.
+ * A stencil reaching beyond nearest grid neighbours breaks the geometric
+ * dissection and gives EINVAL.                                                 */
+int  zolo_analyze(const zolo_csr *A, const zolo_csr *B, const zolo_opts *opts, zolo_symbolic *out);
+int  zolo_symbolic_get_info(zolo_symbolic s, zolo_symbolic_info *out);
+/* Export the index arrays (host buffers sized from the info): perm[n] (new -> old),
+ * first[nnodes], npiv[nnodes], parent[nnodes] (-1 at the root), uptr[nnodes+1] and
+ * urows[uptr[nnodes]] (update rows in new numbering, ascending per front). Any
+ * pointer may be NULL to skip that array.                                        */
+int  zolo_symbolic_export(zolo_symbolic s, int32_t *perm, int32_t *first, int32_t *npiv,
+                          int32_t *parent, int64_t *uptr, int32_t *urows);
+void zolo_symbolic_destroy(zolo_symbolic s);
+
+/* ---- numeric factorisation (device) ------------------------------------- */
+/* Upload the pencil and factor K_j = A - sigma_hat_j B, j = 1..r1, by the multifrontal
+ * method on the device (Algorithm 2 line 5): no-pivot LU of every front, level by
+ * level, with the poles batched in each launch.  `sym` may be NULL (analysed here).
+ * ESINGULAR on a zero / non-finite pivot.  Synchronises `stream`.               */
+int  zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbolic sym,
+                 const zolo_opts *opts, void *stream, zolo_factor_h *out);
+/* Re-factor an existing handle in place (same pencil, filter, options): the timed
+ * factorisation step of a repeated workload.                                     */
+int  zolo_refactor(zolo_factor_h h, void *stream);
+void zolo_factor_destroy(zolo_factor_h h);
+int  zolo_factor_get_stats(zolo_factor_h h, zolo_stats *out);
+
+/* X := K_pole^-1 Bk (herm = 0) or K_pole^-H Bk (herm = 1) for an n x k device block,
+ * through the stored factors (with refinement in MIXED precision).  Bk and X may not
+ * overlap.  0 <= pole < r1.                                                      */
+int  zolo_solve(zolo_factor_h h, int32_t pole, int32_t herm, int64_t k, const void *Bk,
+                int64_t ldb, void *X, int64_t ldx, void *stream);
+/* Y := A X (which = 0) or B X (which = 1), device blocks (SpMM with the uploaded CSR). */
+int  zolo_matmul(zolo_factor_h h, int32_t which, int64_t k, const void *X, int64_t ldx,
+                 void *Y, int64_t ldy, void *stream);
+/* Y := G X, the inner operator of eq. solve (r1 factored poles, conjugates via K^-H). */
+int  zolo_apply_inner(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y,
+                      int64_t ldy, void *stream);
+/* Y := R_ab(B^-1 A) X by Algorithm 2 lines 9-10 (shift-invariant GMRES, one basis per
+ * column shared by the 2 r2 shifts).  X, Y: n x k device blocks, may not overlap.  */
+int  zolo_apply(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                zolo_stats *stats, void *stream);
+
+/* ---- the eigensolver (Algorithm 1 with Algorithm 2 as the filter) ------- */
+/* Eigenpairs of (A, B) in (a, b) for an existing factor handle (its filter fixes the
+ * gaps).  k0: subspace dimension (n_est estimate -> opts).  Results: evals[cap]
+ * ascending (host), evecs n x cap device block (row-major, ld = ldv, B-orthonormal),
+ * resid[cap] host residuals ||A x - lam B x||/(||A||_inf ||x||).  X0 (device, n x k0,
+ * ld = k0) is the starting block, or NULL for the seeded normal block.  On ENOCONV the
+ * best pairs found are still returned.                                          */
+int  zolo_eigs_factored(zolo_factor_h h, double a, double b, int64_t k0, const void *X0,
+                        double *evals, void *evecs, int64_t ldv, int64_t cap, int64_t *n_found,
+                        double *resid, zolo_stats *stats, void *stream);
+/* One-call driver: filter from (a, b) and opts (gaps at gap_rel unless `spec` is given),
+ * analysis, factorisation, Algorithm 1.  spec may be NULL.                      */
+int  zolo_eigs(const zolo_csr *A, const zolo_csr *B, double a, double b, int64_t n_est,
+               const zolo_filter_spec *spec, const zolo_opts *opts, double *evals, void *evecs,
+               int64_t ldv, int64_t cap, int64_t *n_found, double *resid, zolo_stats *stats,
+               void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZOLO_H */

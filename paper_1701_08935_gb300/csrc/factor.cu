@@ -1,0 +1,917 @@
+// Multifrontal factorisation of K_j = A - sigma_hat_j B (Algorithm 2 line 5) and the
+// block triangular solves with K_j and K_j^H that eq. solve needs, on the device.
+//
+// Fronts are dense column-major (pivots, update rows)^2 blocks, stored level by level in
+// one pool per pole.  A level is factored with a right-looking blocked LU without
+// pivoting (panel width NB): per step, the FP64 LU of the diagonal block plus the
+// explicit inverses of its triangles, then L21 = A21 U11^-1 and U12 = L11^-1 A12, then
+// the Schur update A22 -= L21 U12.  After the last pivot block the lower-right block
+// holds the update matrix, which the parent front adds in (extend-add) before its own
+// elimination.  The solves walk the same tree: forward (L y = b, or U^H y = b) from
+// the leaves, children passing their update vectors to the parent, and backward
+// (U x = y, or L^H x = y) from the root, gathering the ancestors' solution rows.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include "factor.h"
+
+namespace zolo {
+
+int cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return ZOLO_OK;
+    return set_error(e == cudaErrorMemoryAllocation ? ZOLO_ENOMEM : ZOLO_ECUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int dev_alloc(zolo_factor_s *h, size_t bytes, void **out) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ZOLO_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    h->owned.push_back(Buf{p, bytes});
+    *out = p;
+    return ZOLO_OK;
+}
+
+static void dev_free(zolo_factor_s *h, void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < h->owned.size(); ++i)
+        if (h->owned[i].p == p) {
+            cudaFree(p);
+            h->owned.erase(h->owned.begin() + i);
+            return;
+        }
+}
+
+namespace {
+
+template <class V> int upload(zolo_factor_s *h, const std::vector<V> &v, V **out) {
+    int st = dev_alloc(h, v.size() * sizeof(V), (void **)out);
+    if (st) return st;
+    if (!v.empty()) return cuda_check(cudaMemcpy(*out, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice), "upload");
+    return ZOLO_OK;
+}
+
+GJob make_job(int64_t a, int ars, int acs, int64_t b, int brs, int bcs, int64_t c, int crs, int ccs, int m, int n,
+              int k, int flags) {
+    GJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.a = a; j.ars = ars; j.acs = acs;
+    j.b = b; j.brs = brs; j.bcs = bcs;
+    j.c = c; j.crs = crs; j.ccs = ccs;
+    j.m = m; j.n = n; j.k = k;
+    j.flags = flags;
+    j.tm = (m + 63) / 64;
+    return j;
+}
+
+// append a launch of GEMM jobs (empty products dropped) and return its descriptor
+Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs) {
+    Launch L;
+    L.off = (int64_t)all.size();
+    int tiles = 0;
+    for (GJob j : jobs) {
+        if (j.m <= 0 || j.n <= 0 || j.k <= 0) continue;
+        j.tile0 = tiles;
+        tiles += j.tm * ((j.n + 63) / 64);
+        all.push_back(j);
+        L.cnt++;
+    }
+    L.ntiles = tiles;
+    return L;
+}
+
+Launch add_rows(std::vector<RJob> &all, const std::vector<RJob> &jobs, int tile_rows) {
+    Launch L;
+    L.off = (int64_t)all.size();
+    int tiles = 0;
+    for (RJob j : jobs) {
+        if (j.rows <= 0) continue;
+        j.tile0 = tiles;
+        j.tr = (j.rows + tile_rows - 1) / tile_rows;
+        tiles += (tile_rows == 32) ? j.tr * j.tr : j.tr;   // 32: square extend-add tiles
+        all.push_back(j);
+        L.cnt++;
+    }
+    L.ntiles = tiles;
+    return L;
+}
+
+RJob rjob(int64_t src, int64_t dst, int64_t map, int rows, int ld_src = 0, int ld_dst = 0) {
+    RJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.src = src; j.dst = dst; j.map = map; j.rows = rows; j.ld_src = ld_src; j.ld_dst = ld_dst;
+    return j;
+}
+
+int check_hermitian(const zolo_csr *M, const char *name, double &norm_inf) {
+    const bool c = (M->dtype == ZOLO_C128);
+    const double *v = (const double *)M->val;
+    double amax = 0.0;
+    norm_inf = 0.0;
+    for (int64_t i = 0; i < M->n; ++i) {
+        double rs = 0.0;
+        for (int64_t p = M->row_ptr[i]; p < M->row_ptr[i + 1]; ++p) {
+            const double re = c ? v[2 * p] : v[p], im = c ? v[2 * p + 1] : 0.0;
+            const double a = std::hypot(re, im);
+            rs += a;
+            amax = std::max(amax, a);
+        }
+        norm_inf = std::max(norm_inf, rs);
+    }
+    const double tol = 1e-12 * std::max(amax, 1e-300);
+    for (int64_t i = 0; i < M->n; ++i) {
+        for (int64_t p = M->row_ptr[i]; p < M->row_ptr[i + 1]; ++p) {
+            const int32_t j = M->col_idx[p];
+            const int32_t *b = M->col_idx + M->row_ptr[j], *e = M->col_idx + M->row_ptr[j + 1];
+            const int32_t *it = std::lower_bound(b, e, (int32_t)i);
+            if (it == e || *it != i) return set_error(ZOLO_ENOTHERM, std::string(name) + ": pattern not symmetric");
+            const int64_t q = M->row_ptr[j] + (it - b);
+            const double re1 = c ? v[2 * p] : v[p], im1 = c ? v[2 * p + 1] : 0.0;
+            const double re2 = c ? v[2 * q] : v[q], im2 = c ? v[2 * q + 1] : 0.0;
+            if (std::fabs(re1 - re2) > tol || std::fabs(im1 + im2) > tol)
+                return set_error(ZOLO_ENOTHERM, std::string(name) + " is not Hermitian");
+        }
+    }
+    return ZOLO_OK;
+}
+
+int upload_csr(zolo_factor_s *h, const zolo_csr *M, DevCSR &D) {
+    D.n = M->n;
+    D.nnz = M->nnz;
+    std::vector<int64_t> rp(M->row_ptr, M->row_ptr + M->n + 1);
+    std::vector<int32_t> ci(M->col_idx, M->col_idx + M->nnz);
+    std::vector<c128> v(M->nnz);
+    const double *src = (const double *)M->val;
+    for (int64_t p = 0; p < M->nnz; ++p)
+        v[p] = (M->dtype == ZOLO_C128) ? c128{src[2 * p], src[2 * p + 1]} : c128{src[p], 0.0};
+    int st = upload(h, rp, &D.rp);
+    if (!st) st = upload(h, ci, &D.ci);
+    if (!st) st = upload(h, v, &D.v);
+    return st;
+}
+
+size_t elem_bytes(int prec) { return prec == ZOLO_PREC_MIXED ? sizeof(c64) : sizeof(c128); }
+
+// ---- layout, assembly maps and the factorisation schedule
+int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
+    const zolo_symbolic_s &S = h->sym;
+    const int nn = S.nnodes;
+    h->f_off.assign(nn, 0);
+    h->f_inv.assign(nn, 0);
+    h->f_wrow.assign(nn, 0);
+    h->f_rows.assign(nn, 0);
+    h->f_rel.assign(nn, -1);
+    int64_t po = 0, io = 0, wo = 0;
+    std::vector<int32_t> rows;
+    rows.reserve(S.n + S.urows.size());
+    for (int idx = 0; idx < nn; ++idx) {
+        const int s = S.by_level[idx];
+        const int64_t nf = S.nf(s), np = S.npiv[s];
+        h->f_off[s] = po;
+        po += nf * nf;
+        h->f_inv[s] = io;
+        io += ((np + NB - 1) / NB) * 2 * NB * NB;
+        h->f_wrow[s] = wo;
+        wo += nf;
+        h->f_rows[s] = (int64_t)rows.size();
+        for (int64_t r = 0; r < np; ++r) rows.push_back(S.perm[S.first[s] + r]);
+        for (int64_t p = S.uptr[s]; p < S.uptr[s + 1]; ++p) rows.push_back(S.perm[S.urows[p]]);
+    }
+    h->pool_elems = po;
+    h->inv_elems = io;
+    h->wrows = wo;
+    // extend-add maps: child update row -> position in the parent front
+    std::vector<int32_t> rel;
+    for (int c = 0; c < nn; ++c) {
+        const int p = S.parent[c];
+        if (p < 0 || S.nu(c) == 0) continue;
+        h->f_rel[c] = (int64_t)rel.size();
+        for (int64_t q = S.uptr[c]; q < S.uptr[c + 1]; ++q) {
+            const int32_t pos = S.pos_in(p, S.urows[q]);
+            if (pos < 0) return set_error(ZOLO_EINVAL, "internal: child update row missing from parent front");
+            rel.push_back(pos);
+        }
+    }
+    int st = upload(h, rows, &h->d_rows);
+    if (!st) st = upload(h, rel, &h->d_rel);
+    if (st) return st;
+    // assembly maps of the original entries, grouped by level of their front
+    std::vector<int32_t> node_of(S.n);
+    for (int s = 0; s < nn; ++s)
+        for (int t = S.first[s]; t < S.first[s] + S.npiv[s]; ++t) node_of[t] = s;
+    const int nl = S.nlevels;
+    h->flev.assign(nl, FLevel());
+    std::vector<int64_t> asmv;
+    auto build_asm = [&](const zolo_csr *M, bool isA) -> int {
+        std::vector<std::vector<std::pair<int64_t, int64_t>>> per(nl);
+        for (int64_t i = 0; i < M->n; ++i) {
+            for (int64_t p = M->row_ptr[i]; p < M->row_ptr[i + 1]; ++p) {
+                const int32_t pi = S.iperm[i], pj = S.iperm[M->col_idx[p]];
+                const int s = node_of[std::min(pi, pj)];
+                const int32_t r = S.pos_in(s, pi), c = S.pos_in(s, pj);
+                if (r < 0 || c < 0) return set_error(ZOLO_EINVAL, "internal: entry outside its front");
+                per[S.level[s]].push_back({p, h->f_off[s] + r + (int64_t)c * S.nf(s)});
+            }
+        }
+        const int64_t base = (int64_t)asmv.size();
+        std::vector<int64_t> src, dst;
+        for (int L = 0; L < nl; ++L) {
+            (isA ? h->flev[L].asmA_lo : h->flev[L].asmB_lo) = (int64_t)src.size();
+            for (auto &e : per[L]) {
+                src.push_back(e.first);
+                dst.push_back(e.second);
+            }
+            (isA ? h->flev[L].asmA_hi : h->flev[L].asmB_hi) = (int64_t)src.size();
+        }
+        (isA ? h->nA_asm : h->nB_asm) = (int64_t)src.size();
+        asmv.insert(asmv.end(), src.begin(), src.end());
+        asmv.insert(asmv.end(), dst.begin(), dst.end());
+        (void)base;
+        return ZOLO_OK;
+    };
+    st = build_asm(A, true);
+    if (!st) st = build_asm(B, false);
+    if (!st) st = upload(h, asmv, &h->d_asm);
+    if (st) return st;
+    // schedule
+    std::vector<DJob> dj;
+    std::vector<GJob> gj;
+    std::vector<RJob> ej;
+    for (int L = 0; L < nl; ++L) {
+        FLevel &F = h->flev[L];
+        const int b = S.level_ptr[L], e = S.level_ptr[L + 1];
+        const int s0 = S.by_level[b], s1 = S.by_level[e - 1];
+        F.pool_lo = h->f_off[s0];
+        F.pool_hi = h->f_off[s1] + (int64_t)S.nf(s1) * S.nf(s1);
+        // extend-add, one launch per child slot (fronts of one launch have distinct parents)
+        size_t maxkids = 0;
+        for (int i = b; i < e; ++i) maxkids = std::max(maxkids, S.children[S.by_level[i]].size());
+        for (size_t slot = 0; slot < maxkids; ++slot) {
+            std::vector<RJob> jobs;
+            for (int i = b; i < e; ++i) {
+                const int p = S.by_level[i];
+                if (slot >= S.children[p].size()) continue;
+                const int c = S.children[p][slot];
+                const int nu = S.nu(c), np = S.npiv[c], nf = S.nf(c);
+                if (nu == 0) continue;
+                jobs.push_back(rjob(h->f_off[c] + np + (int64_t)np * nf, h->f_off[p], h->f_rel[c], nu, nf, S.nf(p)));
+            }
+            F.eadd.push_back(add_rows(ej, jobs, 32));
+        }
+        int maxnp = 0;
+        for (int i = b; i < e; ++i) maxnp = std::max(maxnp, S.npiv[S.by_level[i]]);
+        for (int t = 0; t * NB < maxnp; ++t) {
+            FStep stp;
+            std::vector<DJob> dd;
+            std::vector<GJob> pL, pU, sc;
+            const int kb = t * NB;
+            for (int i = b; i < e; ++i) {
+                const int s = S.by_level[i];
+                const int np = S.npiv[s], nf = S.nf(s);
+                if (np <= kb) continue;
+                const int nb = std::min(NB, np - kb);
+                const int64_t o = h->f_off[s];
+                const int64_t iv = h->f_inv[s] + (int64_t)t * 2 * NB * NB;
+                DJob d;
+                std::memset(&d, 0, sizeof(d));
+                d.off = o + kb + (int64_t)kb * nf;
+                d.inv = iv;
+                d.ld = nf;
+                d.nb = nb;
+                d.front = s;
+                dd.push_back(d);
+                const int rest = nf - kb - nb;
+                // L21 = A21 Uinv   (A: pool, B: inverse store, C aliases A; n = nb <= BN)
+                pL.push_back(make_job(o + kb + nb + (int64_t)kb * nf, 1, nf, iv + NB * NB, 1, NB,
+                                      o + kb + nb + (int64_t)kb * nf, 1, nf, rest, nb, nb, 0));
+                // U12 = Linv A12   (A: inverse store, B: pool, C aliases B; m = nb <= BM)
+                pU.push_back(make_job(iv, 1, NB, o + kb + (int64_t)(kb + nb) * nf, 1, nf,
+                                      o + kb + (int64_t)(kb + nb) * nf, 1, nf, nb, rest, nb, 0));
+                // A22 -= L21 U12
+                sc.push_back(make_job(o + kb + nb + (int64_t)kb * nf, 1, nf, o + kb + (int64_t)(kb + nb) * nf, 1, nf,
+                                      o + kb + nb + (int64_t)(kb + nb) * nf, 1, nf, rest, rest, nb, GJ_SUB));
+            }
+            stp.diag.off = (int64_t)dj.size();
+            stp.diag.cnt = (int)dd.size();
+            stp.diag.ntiles = (int)dd.size();
+            dj.insert(dj.end(), dd.begin(), dd.end());
+            stp.panelL = add_gemm(gj, pL);
+            stp.panelU = add_gemm(gj, pU);
+            stp.schur = add_gemm(gj, sc);
+            F.steps.push_back(stp);
+        }
+    }
+    st = upload(h, dj, &h->d_djobs);
+    if (!st) st = upload(h, gj, &h->d_fjobs);
+    if (!st) st = upload(h, ej, &h->d_ejobs);
+    h->n_djobs = (int64_t)dj.size();
+    if (!st) st = dev_alloc(h, std::max<int64_t>(1, h->n_djobs) * h->r1 * sizeof(double), (void **)&h->d_minpiv);
+    if (!st) st = dev_alloc(h, sizeof(int), (void **)&h->d_err);
+    return st;
+}
+
+template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
+    const int np_ = h->r1;
+    const size_t eb = sizeof(cx<T>);
+    int rc = cuda_check(cudaMemsetAsync(h->d_err, 0, sizeof(int), st), "memset err");
+    if (rc) return rc;
+    const int64_t *asrcA = h->d_asm, *adstA = h->d_asm + h->nA_asm;
+    const int64_t *asrcB = h->d_asm + 2 * h->nA_asm, *adstB = asrcB + h->nB_asm;
+    for (int p0 = 0; p0 < np_; p0 += MAX_INST) {
+        const int ni = std::min(MAX_INST, np_ - p0);
+        cx<T> *pool[MAX_INST], *inv[MAX_INST];
+        for (int z = 0; z < ni; ++z) {
+            pool[z] = (cx<T> *)h->pool[p0 + z];
+            inv[z] = (cx<T> *)h->inv[p0 + z];
+        }
+        for (const FLevel &F : h->flev) {
+            for (int z = 0; z < ni; ++z) {
+                rc = cuda_check(cudaMemsetAsync(pool[z] + F.pool_lo, 0, (F.pool_hi - F.pool_lo) * eb, st), "memset front");
+                if (rc) return rc;
+            }
+            AsmArgs<T> aa;
+            std::memset(&aa, 0, sizeof(aa));
+            for (int z = 0; z < ni; ++z) aa.pool[z] = pool[z];
+            aa.val = h->A.v;
+            aa.src = asrcA + F.asmA_lo;
+            aa.dst = adstA + F.asmA_lo;
+            aa.count = F.asmA_hi - F.asmA_lo;
+            for (int z = 0; z < ni; ++z) aa.scale[z] = c128{1.0, 0.0};
+            launch_assemble<T>(aa, ni, st);
+            aa.val = h->B.v;
+            aa.src = asrcB + F.asmB_lo;
+            aa.dst = adstB + F.asmB_lo;
+            aa.count = F.asmB_hi - F.asmB_lo;
+            for (int z = 0; z < ni; ++z)
+                aa.scale[z] = c128{-h->fi.sigma_hat[2 * (p0 + z)], -h->fi.sigma_hat[2 * (p0 + z) + 1]};
+            launch_assemble<T>(aa, ni, st);
+            for (const Launch &E : F.eadd) {
+                EaddArgs<T> ea;
+                std::memset(&ea, 0, sizeof(ea));
+                ea.jobs = h->d_ejobs + E.off;
+                ea.njobs = E.cnt;
+                ea.ntiles = E.ntiles;
+                ea.rel = h->d_rel;
+                for (int z = 0; z < ni; ++z) ea.pool[z] = pool[z];
+                launch_extend_add<T>(ea, ni, st);
+            }
+            for (const FStep &S : F.steps) {
+                DiagArgs<T> da;
+                std::memset(&da, 0, sizeof(da));
+                da.jobs = h->d_djobs + S.diag.off;
+                da.njobs = S.diag.cnt;
+                da.err = h->d_err;
+                da.minpiv = h->d_minpiv + S.diag.off * np_ + (int64_t)p0 * S.diag.cnt;
+                for (int z = 0; z < ni; ++z) {
+                    da.pool[z] = pool[z];
+                    da.inv[z] = inv[z];
+                }
+                launch_diag_lu<T>(da, ni, st);
+                auto gemm = [&](const Launch &L, int abase, int bbase) {
+                    if (!L.cnt) return;
+                    GemmArgs<T> g;
+                    std::memset(&g, 0, sizeof(g));
+                    for (int z = 0; z < ni; ++z) {
+                        g.jobs[z] = h->d_fjobs + L.off;
+                        g.njobs[z] = L.cnt;
+                        g.ntiles[z] = L.ntiles;
+                        g.A[z] = abase ? inv[z] : pool[z];
+                        g.B[z] = bbase ? inv[z] : pool[z];
+                        g.C[z] = pool[z];
+                    }
+                    launch_gemm<T>(g, ni, st);
+                };
+                gemm(S.panelL, 0, 1);   // L21 = A21 Uinv
+                gemm(S.panelU, 1, 0);   // U12 = Linv A12
+                gemm(S.schur, 0, 0);    // A22 -= L21 U12
+            }
+        }
+    }
+    return cuda_check(cudaGetLastError(), "factor launch");
+}
+
+}  // namespace
+
+int factor_numeric(zolo_factor_s *h, cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    int rc = (h->prec == ZOLO_PREC_MIXED) ? run_factor<float>(h, st) : run_factor<double>(h, st);
+    cudaEventRecord(e1, st);
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "factor");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    h->stats.t_factor_ms = ms;
+    int err = 0;
+    rc = cuda_check(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "err copy");
+    if (rc) return rc;
+    std::vector<double> mp(std::max<int64_t>(1, h->n_djobs) * h->r1);
+    rc = cuda_check(cudaMemcpy(mp.data(), h->d_minpiv, mp.size() * sizeof(double), cudaMemcpyDeviceToHost), "minpiv");
+    if (rc) return rc;
+    double m = 1e300;
+    for (int64_t i = 0; i < h->n_djobs * h->r1; ++i) m = std::min(m, mp[i]);
+    h->stats.min_pivot = m;
+    if (err) return set_error(ZOLO_ESINGULAR, "zero or non-finite pivot in a front");
+    return ZOLO_OK;
+}
+
+// ---- solve schedule for a block width k
+int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
+    if (h->k_sched == k) return ZOLO_OK;
+    const zolo_symbolic_s &S = h->sym;
+    std::vector<GJob> gj;
+    std::vector<RJob> rj;
+    h->fwd.clear();
+    h->bwd.clear();
+    const int K = (int)k;
+    const int nl = S.nlevels;
+    auto gemm_op = [&](std::vector<GJob> &n, std::vector<GJob> &hh, int abase) {
+        SOp o;
+        o.kind = SOP_GEMM;
+        o.abase = abase;
+        o.L = add_gemm(gj, n);
+        o.LH = add_gemm(gj, hh);
+        return o;
+    };
+    for (int L = 0; L < nl; ++L) {                 // forward: leaves to root
+        const int b = S.level_ptr[L], e = S.level_ptr[L + 1];
+        std::vector<RJob> g;
+        for (int i = b; i < e; ++i) {
+            const int s = S.by_level[i];
+            g.push_back(rjob(0, h->f_wrow[s] * k, h->f_rows[s], S.npiv[s]));
+        }
+        SOp og;
+        og.kind = SOP_GATHER_IN;
+        og.L = add_rows(rj, g, ROWS_PER_TILE);
+        h->fwd.push_back(og);
+        size_t maxkids = 0;
+        for (int i = b; i < e; ++i) maxkids = std::max(maxkids, S.children[S.by_level[i]].size());
+        for (size_t slot = 0; slot < maxkids; ++slot) {
+            std::vector<RJob> ea;
+            for (int i = b; i < e; ++i) {
+                const int p = S.by_level[i];
+                if (slot >= S.children[p].size()) continue;
+                const int c = S.children[p][slot];
+                if (S.nu(c) == 0) continue;
+                ea.push_back(rjob((h->f_wrow[c] + S.npiv[c]) * k, h->f_wrow[p] * k, h->f_rel[c], S.nu(c)));
+            }
+            SOp oe;
+            oe.kind = SOP_EADD;
+            oe.L = add_rows(rj, ea, ROWS_PER_TILE);
+            h->fwd.push_back(oe);
+        }
+        int maxnp = 0;
+        for (int i = b; i < e; ++i) maxnp = std::max(maxnp, S.npiv[S.by_level[i]]);
+        for (int t = 0; t * NB < maxnp; ++t) {
+            const int kb = t * NB;
+            std::vector<GJob> iN, iH, uN, uH;
+            for (int i = b; i < e; ++i) {
+                const int s = S.by_level[i];
+                const int np = S.npiv[s], nf = S.nf(s);
+                if (np <= kb) continue;
+                const int nb = std::min(NB, np - kb);
+                const int64_t iv = h->f_inv[s] + (int64_t)t * 2 * NB * NB, o = h->f_off[s];
+                const int64_t w = (h->f_wrow[s] + kb) * k;
+                iN.push_back(make_job(iv, 1, NB, w, K, 1, w, K, 1, nb, K, nb, 0));                      // Linv
+                iH.push_back(make_job(iv + NB * NB, NB, 1, w, K, 1, w, K, 1, nb, K, nb, GJ_CONJA));      // Uinv^H
+                const int rest = nf - kb - nb;
+                const int64_t wc = (h->f_wrow[s] + kb + nb) * k;
+                uN.push_back(make_job(o + kb + nb + (int64_t)kb * nf, 1, nf, w, K, 1, wc, K, 1, rest, K, nb, GJ_SUB));
+                uH.push_back(make_job(o + kb + (int64_t)(kb + nb) * nf, nf, 1, w, K, 1, wc, K, 1, rest, K, nb,
+                                      GJ_SUB | GJ_CONJA));
+            }
+            h->fwd.push_back(gemm_op(iN, iH, 1));
+            h->fwd.push_back(gemm_op(uN, uH, 0));
+        }
+    }
+    for (int L = nl - 1; L >= 0; --L) {           // backward: root to leaves
+        const int b = S.level_ptr[L], e = S.level_ptr[L + 1];
+        std::vector<RJob> g;
+        std::vector<GJob> aN, aH;
+        int maxblk = 0;
+        for (int i = b; i < e; ++i) {
+            const int s = S.by_level[i];
+            const int np = S.npiv[s], nu = S.nu(s), nf = S.nf(s);
+            maxblk = std::max(maxblk, (np + NB - 1) / NB);
+            if (nu == 0) continue;
+            g.push_back(rjob(0, (h->f_wrow[s] + np) * k, h->f_rows[s] + np, nu));
+            const int64_t o = h->f_off[s];
+            const int64_t wu = (h->f_wrow[s] + np) * k, wp = h->f_wrow[s] * k;
+            aN.push_back(make_job(o + (int64_t)np * nf, 1, nf, wu, K, 1, wp, K, 1, np, K, nu, GJ_SUB));
+            aH.push_back(make_job(o + np, nf, 1, wu, K, 1, wp, K, 1, np, K, nu, GJ_SUB | GJ_CONJA));
+        }
+        SOp og;
+        og.kind = SOP_GATHER_OUT;
+        og.L = add_rows(rj, g, ROWS_PER_TILE);
+        h->bwd.push_back(og);
+        h->bwd.push_back(gemm_op(aN, aH, 0));
+        for (int t = 0; t < maxblk; ++t) {
+            std::vector<GJob> iN, iH, uN, uH;
+            for (int i = b; i < e; ++i) {
+                const int s = S.by_level[i];
+                const int np = S.npiv[s], nf = S.nf(s);
+                const int nblk = (np + NB - 1) / NB;
+                if (nblk <= t) continue;
+                const int bi = nblk - 1 - t;
+                const int kb = bi * NB, nb = std::min(NB, np - kb);
+                const int64_t iv = h->f_inv[s] + (int64_t)bi * 2 * NB * NB, o = h->f_off[s];
+                const int64_t w = (h->f_wrow[s] + kb) * k, w0 = h->f_wrow[s] * k;
+                iN.push_back(make_job(iv + NB * NB, 1, NB, w, K, 1, w, K, 1, nb, K, nb, 0));            // Uinv
+                iH.push_back(make_job(iv, NB, 1, w, K, 1, w, K, 1, nb, K, nb, GJ_CONJA));               // Linv^H
+                uN.push_back(make_job(o + (int64_t)kb * nf, 1, nf, w, K, 1, w0, K, 1, kb, K, nb, GJ_SUB));
+                uH.push_back(make_job(o + kb, nf, 1, w, K, 1, w0, K, 1, kb, K, nb, GJ_SUB | GJ_CONJA));
+            }
+            h->bwd.push_back(gemm_op(iN, iH, 1));
+            h->bwd.push_back(gemm_op(uN, uH, 0));
+        }
+        std::vector<RJob> sc;
+        for (int i = b; i < e; ++i) {
+            const int s = S.by_level[i];
+            sc.push_back(rjob(h->f_wrow[s] * k, 0, h->f_rows[s], S.npiv[s]));
+        }
+        SOp os;
+        os.kind = SOP_SCATTER_OUT;
+        os.L = add_rows(rj, sc, ROWS_PER_TILE);
+        h->bwd.push_back(os);
+    }
+    // device copies: [GJob... | RJob...]
+    if (h->sched_buf.p) {
+        dev_free(h, h->sched_buf.p);
+        h->sched_buf = Buf();
+    }
+    const size_t gb = gj.size() * sizeof(GJob), rb = rj.size() * sizeof(RJob);
+    void *p = nullptr;
+    int rc = dev_alloc(h, gb + rb + 16, &p);
+    if (rc) return rc;
+    h->sched_buf = Buf{p, gb + rb + 16};
+    h->d_sjobs = (GJob *)p;
+    h->d_rjobs = (RJob *)((char *)p + gb);
+    if (gb) rc = cuda_check(cudaMemcpy(h->d_sjobs, gj.data(), gb, cudaMemcpyHostToDevice), "sched");
+    if (!rc && rb) rc = cuda_check(cudaMemcpy(h->d_rjobs, rj.data(), rb, cudaMemcpyHostToDevice), "sched");
+    if (rc) return rc;
+    // workspaces
+    if (h->w_buf.p) {
+        dev_free(h, h->w_buf.p);
+        h->w_buf = Buf();
+    }
+    const size_t per = (size_t)h->wrows * k * elem_bytes(h->prec);
+    rc = dev_alloc(h, per * MAX_INST, &p);
+    if (rc) return rc;
+    h->w_buf = Buf{p, per * MAX_INST};
+    for (int z = 0; z < MAX_INST; ++z) h->W[z] = (char *)p + z * per;
+    h->k_sched = k;
+    return ZOLO_OK;
+}
+
+namespace {
+
+template <class T>
+int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
+              int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st) {
+    const size_t per = (size_t)h->wrows * k * sizeof(cx<T>);
+    for (int z = 0; z < ninst; ++z) {
+        int rc = cuda_check(cudaMemsetAsync(h->W[z], 0, per, st), "memset W");
+        if (rc) return rc;
+    }
+    auto run = [&](const std::vector<SOp> &ops) {
+        for (const SOp &o : ops) {
+            if (o.kind == SOP_GEMM) {
+                GemmArgs<T> g;
+                std::memset(&g, 0, sizeof(g));
+                for (int z = 0; z < ninst; ++z) {
+                    const Launch &L = herm[z] ? o.LH : o.L;
+                    g.jobs[z] = h->d_sjobs + L.off;
+                    g.njobs[z] = L.cnt;
+                    g.ntiles[z] = L.ntiles;
+                    g.A[z] = (const cx<T> *)(o.abase ? h->inv[pole[z]] : h->pool[pole[z]]);
+                    g.B[z] = (const cx<T> *)h->W[z];
+                    g.C[z] = (cx<T> *)h->W[z];
+                }
+                launch_gemm<T>(g, ninst, st);
+            } else {
+                RowArgs<T> r;
+                std::memset(&r, 0, sizeof(r));
+                r.jobs = h->d_rjobs + o.L.off;
+                r.njobs = o.L.cnt;
+                r.ntiles = o.L.ntiles;
+                r.map = (o.kind == SOP_EADD) ? h->d_rel : h->d_rows;
+                r.k = (int)k;
+                r.ldw = k;
+                r.mode = (o.kind == SOP_EADD) ? ROW_EADD : (o.kind == SOP_SCATTER_OUT ? ROW_SCATTER : ROW_GATHER);
+                r.ldx = (o.kind == SOP_GATHER_IN) ? ldin : ldout;
+                for (int z = 0; z < ninst; ++z) {
+                    r.W[z] = (cx<T> *)h->W[z];
+                    r.X[z] = (o.kind == SOP_GATHER_IN) ? const_cast<c128 *>(Xin[z]) : Xout[z];
+                }
+                launch_rows<T>(r, ninst, st);
+            }
+        }
+    };
+    run(h->fwd);
+    run(h->bwd);
+    return cuda_check(cudaGetLastError(), "solve launch");
+}
+
+}  // namespace
+
+int solve_batch(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
+                int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st) {
+    if (ninst > MAX_INST) return set_error(ZOLO_EINVAL, "internal: too many instances");
+    int rc = ensure_solve_schedule(h, k);
+    if (rc) return rc;
+    return (h->prec == ZOLO_PREC_MIXED) ? run_solve<float>(h, ninst, pole, herm, k, Xin, ldin, Xout, ldout, st)
+                                        : run_solve<double>(h, ninst, pole, herm, k, Xin, ldin, Xout, ldout, st);
+}
+
+int ensure_scratch(zolo_factor_s *h, int64_t k, int blocks, c128 **out) {
+    const size_t need = (size_t)blocks * h->n * k * sizeof(c128);
+    if (h->scratch.bytes < need) {
+        if (h->scratch.p) dev_free(h, h->scratch.p);
+        h->scratch = Buf();
+        void *p = nullptr;
+        int rc = dev_alloc(h, need, &p);
+        if (rc) return rc;
+        h->scratch = Buf{p, need};
+    }
+    *out = (c128 *)h->scratch.p;
+    return ZOLO_OK;
+}
+
+int solve_refined(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
+                  int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st, int *n_refine) {
+    if (n_refine) *n_refine = 0;
+    int rc = solve_batch(h, ninst, pole, herm, k, Xin, ldin, Xout, ldout, st);
+    if (rc || h->prec != ZOLO_PREC_MIXED) return rc;
+    // FP64 iterative refinement: r = b - K x (K = A - sigma B, or K^H = A - conj(sigma) B),
+    // dx = K~^-1 r with the complex64 factors, x += dx, until ||r_c|| <= tol ||b_c|| for
+    // every column of every instance.
+    return refine_loop(h, ninst, pole, herm, k, Xin, ldin, Xout, ldout, st, n_refine);
+}
+
+int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
+                int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st, int *n_refine) {
+    const size_t blk = (size_t)h->n * k;
+    const size_t need = 2 * (size_t)ninst * blk * sizeof(c128);
+    if (h->rscratch.bytes < need) {
+        if (h->rscratch.p) dev_free(h, h->rscratch.p);
+        h->rscratch = Buf();
+        void *p = nullptr;
+        int rc = dev_alloc(h, need, &p);
+        if (rc) return rc;
+        h->rscratch = Buf{p, need};
+    }
+    if (h->norms_k < k) {
+        if (h->d_norms) dev_free(h, h->d_norms);
+        int rc = dev_alloc(h, 2 * MAX_INST * k * sizeof(double), (void **)&h->d_norms);
+        if (rc) return rc;
+        h->norms_k = k;
+    }
+    c128 *R = (c128 *)h->rscratch.p, *DX = R + ninst * blk;
+    std::vector<double> hb(ninst * k), hr(ninst * k);
+    for (int z = 0; z < ninst; ++z) launch_colnorm2(h->n, k, Xin[z], ldin, h->d_norms + z * k, st);
+    int rc = cuda_check(cudaMemcpyAsync(hb.data(), h->d_norms, ninst * k * sizeof(double), cudaMemcpyDeviceToHost, st),
+                        "norms");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "norms");
+    if (rc) return rc;
+    const double tol = h->opts.refine_tol > 0 ? h->opts.refine_tol : 1e-13;
+    const int itmax = h->opts.refine_max > 0 ? h->opts.refine_max : 8;
+    for (int it = 0;; ++it) {
+        for (int z = 0; z < ninst; ++z) {
+            LinArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.n = h->n;
+            a.k = k;
+            a.ldy = k;
+            a.Y = R + z * blk;
+            a.nterm = 1;
+            a.coef[0] = c128{1.0, 0.0};
+            a.X[0] = Xin[z];
+            a.ldx[0] = ldin;
+            launch_lincomb(a, st);
+            const c128 sg{h->fi.sigma_hat[2 * pole[z]], h->fi.sigma_hat[2 * pole[z] + 1]};
+            launch_spmm(h->A, k, Xout[z], ldout, R + z * blk, k, c128{-1.0, 0.0}, true, st);
+            launch_spmm(h->B, k, Xout[z], ldout, R + z * blk, k, herm[z] ? conj(sg) : sg, true, st);
+            launch_colnorm2(h->n, k, R + z * blk, k, h->d_norms + z * k, st);
+        }
+        rc = cuda_check(cudaMemcpyAsync(hr.data(), h->d_norms, ninst * k * sizeof(double), cudaMemcpyDeviceToHost, st),
+                        "norms");
+        if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "norms");
+        if (rc) return rc;
+        double worst = 0.0;
+        for (int64_t i = 0; i < ninst * k; ++i) worst = std::max(worst, std::sqrt(hr[i] / std::max(hb[i], 1e-300)));
+        if (worst <= tol) break;
+        if (it >= itmax) return set_error(ZOLO_ENOCONV, "refinement of a shifted solve did not converge (" +
+                                                            std::to_string(worst) + ")");
+        const c128 *rin[MAX_INST];
+        c128 *dout[MAX_INST];
+        for (int z = 0; z < ninst; ++z) {
+            rin[z] = R + z * blk;
+            dout[z] = DX + z * blk;
+        }
+        rc = solve_batch(h, ninst, pole, herm, k, rin, k, dout, k, st);
+        if (rc) return rc;
+        for (int z = 0; z < ninst; ++z) {
+            LinArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.n = h->n;
+            a.k = k;
+            a.ldy = ldout;
+            a.Y = Xout[z];
+            a.nterm = 2;
+            a.coef[0] = c128{1.0, 0.0};
+            a.X[0] = Xout[z];
+            a.ldx[0] = ldout;
+            a.coef[1] = c128{1.0, 0.0};
+            a.X[1] = DX + z * blk;
+            a.ldx[1] = k;
+            launch_lincomb(a, st);
+        }
+        if (n_refine) (*n_refine)++;
+    }
+    return ZOLO_OK;
+}
+
+int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st) {
+    // GX = const_hat X + sum_j ( w_hat_j K_j^-1 B X + conj(w_hat_j) K_j^-H B X )   (eq. solve)
+    const int r1 = h->r1;
+    const int nblk = 1 + 2 * r1;
+    c128 *scr = nullptr;
+    int rc = ensure_scratch(h, k, nblk + 2 * std::min(2 * r1, MAX_INST), &scr);
+    if (rc) return rc;
+    c128 *BX = scr;
+    launch_spmm(h->B, k, X, ldx, BX, k, c128{1.0, 0.0}, false, st);
+    for (int p0 = 0; p0 < 2 * r1; p0 += MAX_INST) {
+        const int ni = std::min(MAX_INST, 2 * r1 - p0);
+        int pole[MAX_INST], herm[MAX_INST];
+        const c128 *in[MAX_INST];
+        c128 *out[MAX_INST];
+        for (int z = 0; z < ni; ++z) {
+            const int q = p0 + z;
+            pole[z] = q / 2;
+            herm[z] = q % 2;
+            in[z] = BX;
+            out[z] = scr + (size_t)(1 + q) * h->n * k;
+        }
+        int nref = 0;
+        rc = solve_refined(h, ni, pole, herm, k, in, k, out, k, st, &nref);
+        if (rc) return rc;
+        h->stats.n_refine_max = std::max(h->stats.n_refine_max, nref);
+    }
+    LinArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = h->n;
+    a.k = k;
+    a.ldy = ldy;
+    a.Y = Y;
+    a.nterm = 0;
+    a.coef[a.nterm] = c128{h->fi.const_hat, 0.0};
+    a.X[a.nterm] = X;
+    a.ldx[a.nterm++] = ldx;
+    // the linear combination kernel takes at most LIN_MAX terms: accumulate in passes
+    for (int j = 0; j < r1; ++j) {
+        const c128 w{h->fi.w_hat[2 * j], h->fi.w_hat[2 * j + 1]};
+        for (int hh = 0; hh < 2; ++hh) {
+            if (a.nterm == LIN_MAX) {
+                launch_lincomb(a, st);
+                a.nterm = 0;
+                a.coef[a.nterm] = c128{1.0, 0.0};
+                a.X[a.nterm] = Y;
+                a.ldx[a.nterm++] = ldy;
+            }
+            a.coef[a.nterm] = hh ? conj(w) : w;
+            a.X[a.nterm] = scr + (size_t)(1 + 2 * j + hh) * h->n * k;
+            a.ldx[a.nterm++] = k;
+        }
+    }
+    launch_lincomb(a, st);
+    return cuda_check(cudaGetLastError(), "apply_inner");
+}
+
+}  // namespace zolo
+
+// ============================================================== ABI
+using namespace zolo;
+
+extern "C" {
+
+int zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbolic sym, const zolo_opts *opts,
+                void *stream, zolo_factor_h *out) {
+    clear_error();
+    if (!out || !f) return set_error(ZOLO_EINVAL, "null argument");
+    *out = nullptr;
+    bool ca, cb;
+    int rc = check_csr(A, "A", ca);
+    if (!rc) rc = check_csr(B, "B", cb);
+    if (rc) return rc;
+    if (A->n != B->n) return set_error(ZOLO_EINVAL, "A and B differ in size");
+    auto *h = new zolo_factor_s();
+    if (opts) h->opts = *opts; else zolo_opts_default(&h->opts);
+    h->prec = h->opts.precision == ZOLO_PREC_MIXED ? ZOLO_PREC_MIXED : ZOLO_PREC_FP64;
+    h->n = A->n;
+    h->cplx = ca || cb;
+    h->fi = f->info;
+    h->r1 = f->info.r1;
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    cudaGetDevice(&h->device);
+    double nb_inf = 0.0;
+    rc = check_hermitian(A, "A", h->normA_inf);
+    if (!rc) rc = check_hermitian(B, "B", nb_inf);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    if (sym) {
+        h->sym = *sym;
+        if (h->sym.n != A->n) {
+            delete h;
+            return set_error(ZOLO_EINVAL, "symbolic analysis is for another size");
+        }
+    } else {
+        rc = analyze(A, B, h->opts, h->sym);
+        if (rc) {
+            delete h;
+            return rc;
+        }
+    }
+    rc = upload_csr(h, A, h->A);
+    if (!rc) rc = upload_csr(h, B, h->B);
+    if (!rc) rc = build_factor_plan(h, A, B);
+    const size_t eb = elem_bytes(h->prec);
+    for (int j = 0; !rc && j < h->r1; ++j) {
+        rc = dev_alloc(h, h->pool_elems * eb, &h->pool[j]);
+        if (!rc) rc = dev_alloc(h, std::max<int64_t>(1, h->inv_elems) * eb, &h->inv[j]);
+    }
+    h->stats.flops_factor = h->sym.info.flops_lu * h->r1;
+    h->stats.flops_solve = 16.0 * (double)h->sym.info.nnz_factor;     // fwd + bwd, complex, per column
+    if (!rc) rc = factor_numeric(h, (cudaStream_t)stream);
+    if (rc) {
+        zolo_factor_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return ZOLO_OK;
+}
+
+int zolo_refactor(zolo_factor_h h, void *stream) {
+    clear_error();
+    if (!h) return set_error(ZOLO_EINVAL, "null handle");
+    return factor_numeric(h, (cudaStream_t)stream);
+}
+
+void zolo_factor_destroy(zolo_factor_h h) {
+    if (!h) return;
+    for (auto &b : h->owned) cudaFree(b.p);
+    h->owned.clear();
+    delete h;
+}
+
+int zolo_factor_get_stats(zolo_factor_h h, zolo_stats *out) {
+    clear_error();
+    if (!h || !out) return set_error(ZOLO_EINVAL, "null argument");
+    *out = h->stats;
+    return ZOLO_OK;
+}
+
+int zolo_solve(zolo_factor_h h, int32_t pole, int32_t herm, int64_t k, const void *Bk, int64_t ldb, void *X,
+               int64_t ldx, void *stream) {
+    clear_error();
+    if (!h || !Bk || !X || k <= 0 || ldb < k || ldx < k || pole < 0 || pole >= h->r1 || (herm != 0 && herm != 1))
+        return set_error(ZOLO_EINVAL, "bad argument");
+    const int p = pole, hh = herm;
+    const c128 *in[1] = {(const c128 *)Bk};
+    c128 *outp[1] = {(c128 *)X};
+    int nref = 0;
+    int rc = solve_refined(h, 1, &p, &hh, k, in, ldb, outp, ldx, (cudaStream_t)stream, &nref);
+    if (rc) return rc;
+    h->stats.n_refine_max = std::max(h->stats.n_refine_max, nref);
+    return cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "solve");
+}
+
+int zolo_matmul(zolo_factor_h h, int32_t which, int64_t k, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                void *stream) {
+    clear_error();
+    if (!h || !X || !Y || k <= 0 || ldx < k || ldy < k || (which != 0 && which != 1))
+        return set_error(ZOLO_EINVAL, "bad argument");
+    launch_spmm(which ? h->B : h->A, k, (const c128 *)X, ldx, (c128 *)Y, ldy, c128{1.0, 0.0}, false,
+                (cudaStream_t)stream);
+    return cuda_check(cudaGetLastError(), "spmm");
+}
+
+int zolo_apply_inner(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y, int64_t ldy, void *stream) {
+    clear_error();
+    if (!h || !X || !Y || k <= 0 || ldx < k || ldy < k) return set_error(ZOLO_EINVAL, "bad argument");
+    int rc = apply_inner(h, k, (const c128 *)X, ldx, (c128 *)Y, ldy, (cudaStream_t)stream);
+    if (rc) return rc;
+    return cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "apply_inner");
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// The factor handle: device copies of the pencil, the multifrontal fronts of the r1
+// shifted matrices and the launch schedules that drive them.  Internal.
+#pragma once
+#include <vector>
+#include "zolo_internal.h"
+#include "kernels.cuh"
+
+namespace zolo {
+
+struct Launch {
+    int64_t off = 0;     // first job in the device job array
+    int cnt = 0;         // jobs
+    int ntiles = 0;      // CTAs
+};
+
+// one step of a level's factorisation: diagonal blocks, the two panels, Schur update
+struct FStep {
+    Launch diag, panelL, panelU, schur;
+};
+
+struct FLevel {
+    int64_t pool_lo = 0, pool_hi = 0;              // the level's fronts are contiguous
+    int64_t asmA_lo = 0, asmA_hi = 0, asmB_lo = 0, asmB_hi = 0;
+    std::vector<Launch> eadd;                      // one per child slot
+    std::vector<FStep> steps;
+};
+
+// one launch of the block solve: rows kernel or GEMM
+struct SOp {
+    int kind = 0;        // SOP_*
+    int abase = 0;       // GEMM: A operand in the front pool (0) or the inverse store (1)
+    Launch L;            // rows jobs, or GEMM jobs for K^-1
+    Launch LH;           // GEMM jobs for K^-H
+};
+enum { SOP_GATHER_IN = 0, SOP_EADD = 1, SOP_GEMM = 2, SOP_GATHER_OUT = 3, SOP_SCATTER_OUT = 4 };
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace zolo
+
+struct zolo_factor_s {
+    int device = 0;
+    int prec = ZOLO_PREC_FP64;
+    int64_t n = 0;
+    int r1 = 0;
+    bool cplx = false;
+    zolo_opts opts;
+    zolo_filter_info fi;
+    zolo_symbolic_s sym;
+    zolo::DevCSR A, B;
+    double normA_inf = 0.0;
+    std::vector<zolo::Buf> owned;                  // every device allocation
+
+    // front layout (per node)
+    std::vector<int64_t> f_off, f_inv, f_wrow, f_rows, f_rel;
+    int64_t pool_elems = 0, inv_elems = 0, wrows = 0;
+    void *pool[ZOLO_MAX_R] = {};                   // per pole: fronts (T)
+    void *inv[ZOLO_MAX_R] = {};                    // per pole: diagonal-block inverses (T)
+    int32_t *d_rows = nullptr, *d_rel = nullptr;
+    int64_t *d_asm = nullptr;                      // [srcA | dstA | srcB | dstB]
+    int64_t nA_asm = 0, nB_asm = 0;
+
+    // factorisation schedule
+    std::vector<zolo::FLevel> flev;
+    zolo::DJob *d_djobs = nullptr;
+    zolo::GJob *d_fjobs = nullptr;
+    zolo::RJob *d_ejobs = nullptr;
+    int64_t n_djobs = 0;
+    double *d_minpiv = nullptr;
+    int *d_err = nullptr;
+
+    // solve schedule (built for one k at a time)
+    int64_t k_sched = -1;
+    std::vector<zolo::SOp> fwd, bwd;
+    zolo::GJob *d_sjobs = nullptr;
+    zolo::RJob *d_rjobs = nullptr;
+    zolo::Buf sched_buf;
+    void *W[zolo::MAX_INST] = {};                  // front workspaces (T), wrows x k each
+    zolo::Buf w_buf;
+
+    // scratch for the inner operator and for refinement (complex128, n x k blocks)
+    zolo::Buf scratch, rscratch;
+    double *d_norms = nullptr;                     // column norms, 2 * MAX_INST * kmax
+    int64_t norms_k = 0;
+
+    zolo_stats stats;
+};
+
+namespace zolo {
+int dev_alloc(zolo_factor_s *h, size_t bytes, void **out);
+int cuda_check(cudaError_t e, const char *what);
+int factor_numeric(zolo_factor_s *h, cudaStream_t st);
+int ensure_solve_schedule(zolo_factor_s *h, int64_t k);
+// Batched block solves: for instance z < ninst, Xout[z] = K_{pole[z]}^{-1} Xin[z] (herm 0)
+// or K^{-H} Xin[z] (herm 1), on the stored factors (no refinement).
+int solve_batch(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
+                int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st);
+// Same with FP64 iterative refinement when the factors are complex64.
+int solve_refined(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
+                  int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st, int *n_refine);
+int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
+                int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st, int *n_refine);
+int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st);
+// scratch block of complex128 with at least `blocks` n x k blocks
+int ensure_scratch(zolo_factor_s *h, int64_t k, int blocks, c128 **out);
+}  // namespace zolo

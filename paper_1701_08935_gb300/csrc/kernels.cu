@@ -1,0 +1,389 @@
+// Kernels of the multifrontal factorisation and the block triangular solves
+// (Section 2.3: K_j = A - sigma_j B factored once, then applied to blocks of vectors),
+// plus the CSR SpMM.  Every kernel is batched: blockIdx.z selects an instance
+// (a pole, or a (pole, K^-1 / K^-H) pair) and job lists built on the host describe
+// all fronts of one tree level, so one launch covers a whole level.
+#include "kernels.cuh"
+
+namespace zolo {
+
+// ============================================================== batched GEMM
+// C (=|-=) op(A) op(B) for every job in the list; one CTA per BM x BN tile.
+// The whole kk extent of a tile is read before its C block is written, so a job
+// whose C aliases A (with n <= BN) or B (with m <= BM) is computed in place.
+template <class T, int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
+    const int z = blockIdx.z;
+    const int tile = blockIdx.x;
+    if (tile >= g.ntiles[z]) return;
+    const GJob *jobs = g.jobs[z];
+    __shared__ int s_job;
+    __shared__ cx<T> As[BK][BM];
+    __shared__ cx<T> Bs[BK][BN];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int lo = 0, hi = g.njobs[z] - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const GJob J = jobs[s_job];
+    const int t = tile - J.tile0;
+    const int i0 = (t % J.tm) * BM, j0 = (t / J.tm) * BN;
+    const cx<T> *__restrict__ A = g.A[z] + J.a;
+    const cx<T> *__restrict__ B = g.B[z] + J.b;
+    const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
+    const int tx = tid & 15, ty = tid >> 4;
+    cx<T> acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = mk<T>(0, 0);
+
+    for (int l0 = 0; l0 < J.k; l0 += BK) {
+        // ---- stage A tile (BM x BK) and B tile (BK x BN)
+#pragma unroll
+        for (int q = 0; q < (BM * BK) / 256; ++q) {
+            const int e = tid + 256 * q;
+            int i, l;
+            if (J.ars == 1) { i = e % BM; l = e / BM; } else { l = e % BK; i = e / BK; }
+            cx<T> v = mk<T>(0, 0);
+            if (i0 + i < J.m && l0 + l < J.k) v = A[(int64_t)(i0 + i) * J.ars + (int64_t)(l0 + l) * J.acs];
+            As[l][i] = conjA ? conj(v) : v;
+        }
+#pragma unroll
+        for (int q = 0; q < (BN * BK) / 256; ++q) {
+            const int e = tid + 256 * q;
+            int j, l;
+            if (J.brs == 1) { l = e % BK; j = e / BK; } else { j = e % BN; l = e / BN; }
+            cx<T> v = mk<T>(0, 0);
+            if (j0 + j < J.n && l0 + l < J.k) v = B[(int64_t)(l0 + l) * J.brs + (int64_t)(j0 + j) * J.bcs];
+            Bs[l][j] = conjB ? conj(v) : v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int l = 0; l < BK; ++l) {
+            cx<T> a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[l][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[l][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) fma_acc(acc[r][c], a[r], b[c]);
+        }
+        __syncthreads();
+    }
+    cx<T> *__restrict__ C = g.C[z] + J.c;
+    const bool sub = J.flags & GJ_SUB;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty + 16 * r;
+        if (i >= J.m) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = j0 + tx + 16 * c;
+            if (j >= J.n) continue;
+            cx<T> *p = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
+            *p = sub ? (*p - acc[r][c]) : acc[r][c];
+        }
+    }
+}
+
+template <class T>
+void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st) {
+    int mx = 0;
+    for (int z = 0; z < ninst; ++z) mx = g.ntiles[z] > mx ? g.ntiles[z] : mx;
+    if (mx == 0) return;
+    dim3 grid(mx, 1, ninst);
+    k_gemm<T, 64, 64, 16><<<grid, 256, 0, st>>>(g);
+}
+
+// ============================================================== diagonal blocks
+// No-pivot LU of an nb x nb diagonal block in FP64 shared memory, then the explicit
+// inverses of its unit-lower L and upper U (one thread per column, substitution).
+// A zero or non-finite pivot sets bit 1 of *err; the block is still written.
+template <class T>
+__global__ void __launch_bounds__(256) k_diag_lu(DiagArgs<T> g) {
+    const int z = blockIdx.z;
+    if ((int)blockIdx.x >= g.njobs) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c128 *blk = reinterpret_cast<c128 *>(smem_raw);          // NB x NB, ld NB
+    c128 *X = blk + NB * NB;                                  // inverse column buffer
+    const DJob J = g.jobs[blockIdx.x];
+    cx<T> *F = g.pool[z] + J.off;
+    const int nb = J.nb, tid = threadIdx.x;
+    for (int e = tid; e < nb * nb; e += 256) {
+        const int i = e % nb, j = e / nb;
+        blk[i + j * NB] = cvt<double>(F[i + (int64_t)j * J.ld]);
+    }
+    __syncthreads();
+    double minpiv = 1e300;
+    for (int p = 0; p < nb; ++p) {
+        const c128 piv = blk[p + p * NB];
+        const double a2 = abs2(piv);
+        if (tid == 0) {
+            minpiv = fmin(minpiv, sqrt(a2));
+            if (!(a2 > 0.0) || !isfinite(a2)) atomicOr(g.err, 1);
+        }
+        const c128 ip = (a2 > 0.0 && isfinite(a2)) ? cdiv(mk<double>(1, 0), piv) : mk<double>(0, 0);
+        for (int i = p + 1 + tid; i < nb; i += 256) blk[i + p * NB] = blk[i + p * NB] * ip;
+        __syncthreads();
+        const int r = nb - p - 1;
+        for (int e = tid; e < r * r; e += 256) {
+            const int i = p + 1 + e % r, j = p + 1 + e / r;
+            blk[i + j * NB] = blk[i + j * NB] - blk[i + p * NB] * blk[p + j * NB];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) g.minpiv[(int64_t)z * g.njobs + blockIdx.x] = minpiv;
+    cx<T> *Li = g.inv[z] + J.inv;
+    cx<T> *Ui = Li + NB * NB;
+    // Linv: column j solves L x = e_j (unit lower)
+    if (tid < nb) {
+        const int j = tid;
+        X[j + j * NB] = mk<double>(1, 0);
+        for (int i = j + 1; i < nb; ++i) {
+            c128 s = mk<double>(0, 0);
+            for (int t = j; t < i; ++t) fma_acc(s, blk[i + t * NB], X[t + j * NB]);
+            X[i + j * NB] = mk<double>(-s.re, -s.im);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += 256) {
+        const int i = e % nb, j = e / nb;
+        Li[i + j * NB] = (i >= j) ? cvt<T>(X[i + j * NB]) : mk<T>(0, 0);
+    }
+    __syncthreads();
+    // Uinv: column j solves U x = e_j (upper)
+    if (tid < nb) {
+        const int j = tid;
+        X[j + j * NB] = cdiv(mk<double>(1, 0), blk[j + j * NB]);
+        for (int i = j - 1; i >= 0; --i) {
+            c128 s = mk<double>(0, 0);
+            for (int t = i + 1; t <= j; ++t) fma_acc(s, blk[i + t * NB], X[t + j * NB]);
+            X[i + j * NB] = cdiv(mk<double>(-s.re, -s.im), blk[i + i * NB]);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += 256) {
+        const int i = e % nb, j = e / nb;
+        Ui[i + j * NB] = (i <= j) ? cvt<T>(X[i + j * NB]) : mk<T>(0, 0);
+        F[i + (int64_t)j * J.ld] = cvt<T>(blk[i + j * NB]);
+    }
+}
+
+template <class T>
+void launch_diag_lu(const DiagArgs<T> &g, int ninst, cudaStream_t st) {
+    if (g.njobs == 0) return;
+    const size_t smem = 2 * NB * NB * sizeof(c128);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_diag_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    dim3 grid(g.njobs, 1, ninst);
+    k_diag_lu<T><<<grid, 256, smem, st>>>(g);
+}
+
+// ============================================================== assembly
+// F[dst[e]] += scale_z * val[src[e]]  (entries of A, then of B with scale -sigma_z)
+template <class T>
+__global__ void k_assemble(AsmArgs<T> g) {
+    const int z = blockIdx.z;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= g.count) return;
+    const c128 v = g.val[g.src[e]];
+    const c128 s = g.scale[z];
+    cx<T> *p = g.pool[z] + g.dst[e];
+    *p = *p + cvt<T>(s * v);
+}
+
+template <class T>
+void launch_assemble(const AsmArgs<T> &g, int ninst, cudaStream_t st) {
+    if (g.count == 0) return;
+    dim3 grid((unsigned)((g.count + 255) / 256), 1, ninst);
+    k_assemble<T><<<grid, 256, 0, st>>>(g);
+}
+
+// ============================================================== matrix extend-add
+// Parent front += child's Schur block, scattered through the child's relative map:
+// F_p[rel[i] + rel[j] ld_p] += F_c[i + j ld_c]  over a 32 x 32 tile per CTA.
+template <class T>
+__global__ void __launch_bounds__(256) k_extend_add(EaddArgs<T> g) {
+    const int z = blockIdx.z;
+    const int tile = blockIdx.x;
+    if (tile >= g.ntiles) return;
+    __shared__ int s_job;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = g.njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const RJob J = g.jobs[s_job];
+    const int t = tile - J.tile0;
+    const int bi = (t % J.tr) * 32, bj = (t / J.tr) * 32;
+    const int32_t *rel = g.rel + J.map;
+    const cx<T> *S = g.pool[z] + J.src;
+    cx<T> *P = g.pool[z] + J.dst;
+    const int i = bi + (threadIdx.x & 31);
+    if (i >= J.rows) return;
+    const int ri = rel[i];
+    for (int jj = threadIdx.x >> 5; jj < 32; jj += 8) {
+        const int j = bj + jj;
+        if (j >= J.rows) break;
+        cx<T> *p = P + ri + (int64_t)rel[j] * J.ld_dst;
+        *p = *p + S[i + (int64_t)j * J.ld_src];
+    }
+}
+
+template <class T>
+void launch_extend_add(const EaddArgs<T> &g, int ninst, cudaStream_t st) {
+    if (g.ntiles == 0) return;
+    dim3 grid(g.ntiles, 1, ninst);
+    k_extend_add<T><<<grid, 256, 0, st>>>(g);
+}
+
+// ============================================================== row moves
+// mode ROW_GATHER : W[dst + r ldw + c]            = X[map[r] ldx + c]     (X c128 -> W T)
+// mode ROW_SCATTER: X[map[r] ldx + c]             = W[src + r ldw + c]    (W T -> X c128)
+// mode ROW_EADD   : W[dst + map[r] ldw + c]      += W[src + r ldw + c]    (child -> parent)
+template <class T>
+__global__ void __launch_bounds__(256) k_rows(RowArgs<T> g) {
+    const int z = blockIdx.z;
+    const int tile = blockIdx.x;
+    if (tile >= g.ntiles) return;
+    __shared__ int s_job;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = g.njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const RJob J = g.jobs[s_job];
+    const int r0 = (tile - J.tile0) * ROWS_PER_TILE;
+    const int32_t *map = g.map + J.map;
+    const int k = g.k;
+    cx<T> *W = g.W[z];
+    c128 *X = g.X[z];
+    for (int e = threadIdx.x; e < ROWS_PER_TILE * k; e += 256) {
+        const int rr = e / k, c = e - rr * k;
+        const int r = r0 + rr;
+        if (r >= J.rows) break;
+        if (g.mode == ROW_GATHER) {
+            W[J.dst + (int64_t)r * g.ldw + c] = cvt<T>(X[(int64_t)map[r] * g.ldx + c]);
+        } else if (g.mode == ROW_SCATTER) {
+            X[(int64_t)map[r] * g.ldx + c] = cvt<double>(W[J.src + (int64_t)r * g.ldw + c]);
+        } else {
+            cx<T> *p = W + J.dst + (int64_t)map[r] * g.ldw + c;
+            *p = *p + W[J.src + (int64_t)r * g.ldw + c];
+        }
+    }
+}
+
+template <class T>
+void launch_rows(const RowArgs<T> &g, int ninst, cudaStream_t st) {
+    if (g.ntiles == 0) return;
+    dim3 grid(g.ntiles, 1, ninst);
+    k_rows<T><<<grid, 256, 0, st>>>(g);
+}
+
+// ============================================================== SpMM
+// Y[i, c] = s * sum_e M[i, col_e] X[col_e, c] (+ Y[i, c] if acc), complex128, row-major
+// blocks.  One warp per row, lanes across the k columns (each nonzero reads a
+// contiguous row of X).
+__global__ void __launch_bounds__(256) k_spmm(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                              const c128 *__restrict__ v, int64_t n, int k,
+                                              const c128 *__restrict__ X, int64_t ldx, c128 *__restrict__ Y,
+                                              int64_t ldy, c128 s, int acc) {
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = rp[row], e = rp[row + 1];
+    for (int c = lane; c < k; c += 32) {
+        c128 sum = mk<double>(0, 0);
+        for (int64_t p = b; p < e; ++p) fma_acc(sum, v[p], X[(int64_t)ci[p] * ldx + c]);
+        c128 *y = Y + row * ldy + c;
+        *y = acc ? (*y + s * sum) : (s * sum);
+    }
+}
+
+void launch_spmm(const DevCSR &M, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, c128 s,
+                 bool acc, cudaStream_t st) {
+    if (M.n == 0 || k == 0) return;
+    dim3 grid((unsigned)((M.n + 7) / 8));
+    k_spmm<<<grid, 256, 0, st>>>(M.rp, M.ci, M.v, M.n, (int)k, X, ldx, Y, ldy, s, acc ? 1 : 0);
+}
+
+// ============================================================== elementwise
+// Y = sum_t coef[t] * X_t   (t < nterm, every operand n x k with its own ld)
+__global__ void k_lincomb(LinArgs a) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.n * a.k) return;
+    const int64_t i = idx / a.k, c = idx - i * a.k;
+    c128 s = mk<double>(0, 0);
+    for (int t = 0; t < a.nterm; ++t) fma_acc(s, a.coef[t], a.X[t][i * a.ldx[t] + c]);
+    a.Y[i * a.ldy + c] = s;
+}
+
+void launch_lincomb(const LinArgs &a, cudaStream_t st) {
+    const int64_t tot = a.n * a.k;
+    if (tot == 0) return;
+    k_lincomb<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a);
+}
+
+// ============================================================== column norms
+// stage 1: CTA b sums rows b, b + G, b + 2G, ... into part[b * k + c];  stage 2 sums parts.
+constexpr int NORM_CTAS = 304;
+__global__ void __launch_bounds__(256) k_colnorm_part(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx,
+                                                      double *__restrict__ part) {
+    for (int c = threadIdx.x; c < k; c += 256) {
+        double s = 0.0;
+        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s += abs2(X[i * ldx + c]);
+        part[(int64_t)blockIdx.x * k + c] = s;
+    }
+}
+__global__ void k_colnorm_sum(int k, int parts, const double *__restrict__ part, double *__restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= k) return;
+    double s = 0.0;
+    for (int b = 0; b < parts; ++b) s += part[(int64_t)b * k + c];
+    out[c] = s;
+}
+
+void launch_colnorm2(int64_t n, int64_t k, const c128 *X, int64_t ldx, double *out, cudaStream_t st) {
+    static double *part = nullptr;
+    static int64_t cap = 0;
+    if (cap < NORM_CTAS * k) {
+        if (part) cudaFree(part);
+        cudaMalloc(&part, NORM_CTAS * k * sizeof(double));
+        cap = NORM_CTAS * k;
+    }
+    k_colnorm_part<<<NORM_CTAS, 256, 0, st>>>(n, (int)k, X, ldx, part);
+    k_colnorm_sum<<<(unsigned)((k + 255) / 256), 256, 0, st>>>((int)k, NORM_CTAS, part, out);
+}
+
+// explicit instantiations
+template void launch_gemm<double>(const GemmArgs<double> &, int, cudaStream_t);
+template void launch_gemm<float>(const GemmArgs<float> &, int, cudaStream_t);
+template void launch_diag_lu<double>(const DiagArgs<double> &, int, cudaStream_t);
+template void launch_diag_lu<float>(const DiagArgs<float> &, int, cudaStream_t);
+template void launch_assemble<double>(const AsmArgs<double> &, int, cudaStream_t);
+template void launch_assemble<float>(const AsmArgs<float> &, int, cudaStream_t);
+template void launch_extend_add<double>(const EaddArgs<double> &, int, cudaStream_t);
+template void launch_extend_add<float>(const EaddArgs<float> &, int, cudaStream_t);
+template void launch_rows<double>(const RowArgs<double> &, int, cudaStream_t);
+template void launch_rows<float>(const RowArgs<float> &, int, cudaStream_t);
+
+}  // namespace zolo

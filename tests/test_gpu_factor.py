@@ -1,0 +1,86 @@
+"""GPU parity of the multifrontal factorisation and block solves (through the C ABI)
+against the oracle's exact sparse solves, plus the SpMM and the inner operator G."""
+import numpy as np
+import pytest
+
+import paper_1701_08935_gb300 as Z
+from oracle import apply as AP
+from oracle import factor as FA
+from oracle import filter as F
+from gpu_common import CASES, case, colrel, dev, host, need_gpu
+from paper_1701_08935_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _factor(name, prec=Z.PREC_FP64, r=(2, 2)):
+    pen, leaf, gaps, lam = case(name)
+    flt = Z.Filter(*gaps, *r)
+    opts = Z.default_opts(grid=pen.dims, leaf_max=leaf, precision=prec)
+    fac = Z.Factor(pen.A, pen.B, flt, opts=opts)
+    return pen, flt, fac, gaps
+
+
+@pytest.mark.parametrize("name", ["real2d_12", "cplx3d_9"])
+@pytest.mark.parametrize("k", [1, 37, 130])
+def test_spmm(name, k):
+    need_gpu()
+    pen, flt, fac, _ = _factor(name)
+    X = synth.random_block(pen.n, k, 11)
+    for which, M in (("A", pen.A), ("B", pen.B)):
+        Y = host(fac.matmul(which, dev(X)))
+        assert colrel(Y, M @ X) < 1e-14
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", [Z.PREC_FP64, Z.PREC_MIXED])
+def test_shifted_solves(name, prec):
+    """X = K_j^-1 b and K_j^-H b for every factored pole against SuperLU."""
+    need_gpu()
+    pen, flt, fac, _ = _factor(name, prec)
+    k = 37
+    Bk = synth.random_block(pen.n, k, 5)
+    for j, s in enumerate(flt.sigma_hat):
+        ref = FA.Solver(pen.A, pen.B, s)
+        for herm in (False, True):
+            X = host(fac.solve(j, dev(Bk), herm=herm))
+            R = ref.solve(Bk, herm=herm)
+            assert colrel(X, R) < 1e-10, (j, herm)
+    st = fac.stats()
+    assert st["min_pivot"] > 0
+    if prec == Z.PREC_MIXED:
+        assert st["n_refine_max"] >= 1
+
+
+@pytest.mark.parametrize("name", ["real2d_40", "cplx3d_12"])
+def test_solve_single_column_and_wide_block(name):
+    need_gpu()
+    pen, flt, fac, _ = _factor(name)
+    ref = FA.Solver(pen.A, pen.B, flt.sigma_hat[0])
+    for k in (1, 65, 200):
+        Bk = synth.random_block(pen.n, k, 100 + k)
+        X = host(fac.solve(0, dev(Bk)))
+        assert colrel(X, ref.solve(Bk)) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["real2d_12", "cplx3d_9", "cplx3d_12"])
+@pytest.mark.parametrize("prec", [Z.PREC_FP64, Z.PREC_MIXED])
+def test_inner_operator(name, prec):
+    """G X = const X + sum_j (w_j K_j^-1 B X + conj(w_j) K_j^-H B X)  (eq. solve)."""
+    need_gpu()
+    pen, flt, fac, gaps = _factor(name, prec)
+    oflt = F.ZoloFilter(*gaps, 2, 2)
+    G = AP.InnerOperator(pen.A, pen.B, oflt)
+    X = synth.random_block(pen.n, 24, 3)
+    Y = host(fac.apply_inner(dev(X)))
+    assert colrel(Y, G(X)) < 1e-10
+
+
+def test_refactor_is_repeatable():
+    need_gpu()
+    pen, flt, fac, _ = _factor("cplx3d_9")
+    Bk = synth.random_block(pen.n, 8, 9)
+    X1 = host(fac.solve(1, dev(Bk), herm=True))
+    fac.refactor()
+    X2 = host(fac.solve(1, dev(Bk), herm=True))
+    assert np.array_equal(X1, X2)
