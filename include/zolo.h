@@ -105,7 +105,7 @@ typedef struct {
                               dense front (only for n <= 8192)                  */
     int32_t  leaf_max;     /* nested-dissection leaf size (default 32)            */
     int32_t  precision;    /* ZOLO_PREC_FP64 (default) or ZOLO_PREC_MIXED         */
-    int32_t  gmres_m_max;  /* GMRES steps at most (default 40)                    */
+    int32_t  gmres_m_max;  /* GMRES steps at most (default 100)                   */
     double   gmres_tol;    /* stop when every shift's least-squares residual is
                               <= gmres_tol * ||x_c|| for every column (default 1e-12) */
     int32_t  refine_max;   /* refinement steps per shifted solve, MIXED (default 8) */

@@ -71,7 +71,7 @@ def _lsq(Hbar, s, beta):
     return z, float(np.linalg.norm(rhs - Hs @ z))
 
 
-def apply_hybrid(A, B, X, flt, tol=1e-12, m_max=40, G=None, return_info=False):
+def apply_hybrid(A, B, X, flt, tol=1e-12, m_max=100, G=None, return_info=False):
     X = np.asarray(X, dtype=np.complex128)
     n, k = X.shape
     G = G if G is not None else InnerOperator(A, B, flt)

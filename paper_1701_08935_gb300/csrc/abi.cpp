@@ -22,7 +22,7 @@ void zolo_opts_default(zolo_opts *o) {
     std::memset(o, 0, sizeof(*o));
     o->leaf_max = 32;
     o->precision = ZOLO_PREC_FP64;
-    o->gmres_m_max = 40;
+    o->gmres_m_max = 100;
     o->gmres_tol = 1e-12;
     o->refine_max = 8;
     o->refine_tol = 1e-13;

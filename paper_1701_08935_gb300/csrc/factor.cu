@@ -37,6 +37,17 @@ int dev_alloc(zolo_factor_s *h, size_t bytes, void **out) {
     return ZOLO_OK;
 }
 
+void dev_release(zolo_factor_s *h, Buf &b) {
+    if (!b.p) return;
+    for (size_t i = 0; i < h->owned.size(); ++i)
+        if (h->owned[i].p == b.p) {
+            cudaFree(b.p);
+            h->owned.erase(h->owned.begin() + i);
+            break;
+        }
+    b = Buf();
+}
+
 static void dev_free(zolo_factor_s *h, void *p) {
     if (!p) return;
     for (size_t i = 0; i < h->owned.size(); ++i)
@@ -869,6 +880,8 @@ int zolo_refactor(zolo_factor_h h, void *stream) {
 
 void zolo_factor_destroy(zolo_factor_h h) {
     if (!h) return;
+    krylov_free(h->kw);
+    h->kw = nullptr;
     for (auto &b : h->owned) cudaFree(b.p);
     h->owned.clear();
     delete h;

@@ -39,6 +39,8 @@ struct Buf {
     size_t bytes = 0;
 };
 
+struct KrylovWork;                                 // GMRES / Rayleigh-Ritz buffers (krylov.cu)
+void krylov_free(KrylovWork *w);
 }  // namespace zolo
 
 struct zolo_factor_s {
@@ -86,11 +88,13 @@ struct zolo_factor_s {
     double *d_norms = nullptr;                     // column norms, 2 * MAX_INST * kmax
     int64_t norms_k = 0;
 
+    zolo::KrylovWork *kw = nullptr;
     zolo_stats stats;
 };
 
 namespace zolo {
 int dev_alloc(zolo_factor_s *h, size_t bytes, void **out);
+void dev_release(zolo_factor_s *h, Buf &b);        // frees b if the handle owns it
 int cuda_check(cudaError_t e, const char *what);
 int factor_numeric(zolo_factor_s *h, cudaStream_t st);
 int ensure_solve_schedule(zolo_factor_s *h, int64_t k);
