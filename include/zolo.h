@@ -106,13 +106,16 @@ typedef struct {
     int32_t  leaf_max;     /* nested-dissection leaf size (default 32)            */
     int32_t  precision;    /* ZOLO_PREC_FP64 (default) or ZOLO_PREC_MIXED         */
     int32_t  gmres_m_max;  /* GMRES steps at most (default 100)                   */
-    double   gmres_tol;    /* stop when every shift's least-squares residual is
-                              <= gmres_tol * ||x_c|| for every column (default 1e-12) */
+    double   gmres_tol;    /* stop when, for every column c, the filtered-column error
+                              bound sum_s |omega_s| res_s / sqrt(l2^2 + |s|^2) is
+                              <= gmres_tol * ||x_c|| (res_s: shift s least-squares
+                              residual; default 1e-12)                           */
     int32_t  refine_max;   /* refinement steps per shifted solve, MIXED (default 8) */
     double   refine_tol;   /* refinement stops at ||b - K x|| <= refine_tol ||b|| (1e-13) */
     int32_t  n_iter_max;   /* subspace iterations at most (default 4)             */
     double   tol;          /* eigenpair residual ||Ax - lam Bx||/(||A||_inf ||x||) (1e-10) */
-    double   drop_tol;     /* B-Gram eigenvalues below drop_tol * max are dropped (1e-14) */
+    double   drop_tol;     /* B-Gram eigenvalues below max(drop_tol, (10 tol_g)^2) * max
+                              are dropped, tol_g the GMRES tolerance of that pass (1e-14) */
     int32_t  k;            /* subspace dimension; <= 0: ceil(1.5 n_est) + 8        */
     int32_t  r1, r2;       /* filter orders used by zolo_eigs (default 2, 2)       */
     double   gap_rel;      /* zolo_eigs without gaps: a- = a - g, b+ = b + g with
@@ -136,6 +139,8 @@ typedef struct {
     double  min_pivot;         /* smallest |pivot| over all fronts and poles    */
     double  flops_factor;      /* algorithmic flops of one factorisation set    */
     double  flops_solve;       /* algorithmic flops of one block solve (k = 1)  */
+    int64_t solve_cols;        /* block-solve columns run since the factorisation
+                                  (instances x columns, refinement included)   */
 } zolo_stats;
 
 typedef struct zolo_filter_s   *zolo_filter;
@@ -188,6 +193,15 @@ void zolo_symbolic_destroy(zolo_symbolic s);
  * ESINGULAR on a zero / non-finite pivot.  Synchronises `stream`.               */
 int  zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbolic sym,
                  const zolo_opts *opts, void *stream, zolo_factor_h *out);
+/* Sylvester inertia: count[i] = number of eigenvalues of (A, B) below the real shift
+ * sigma[i], i.e. the negative inertia of A - sigma_i B, read off the signs of the pivots
+ * of the same no-pivot multifrontal factorisation (eq. IGEVP footnote: n_lambda is only
+ * estimated; counts at a and b give it).  Always complex128 fronts whatever
+ * opts->precision says (complex64 pivot signs are unreliable for indefinite shifts);
+ * nshift >= 1 shifts, factored in batches of at most ZOLO_MAX_R that fit 45% of the
+ * free device memory.  A shift on an eigenvalue gives ESINGULAR.  Synchronises.     */
+int  zolo_inertia(const zolo_csr *A, const zolo_csr *B, zolo_symbolic sym, const zolo_opts *opts,
+                  int32_t nshift, const double *sigma, int64_t *count, void *stream);
 /* Re-factor an existing handle in place (same pencil, filter, options): the timed
  * factorisation step of a repeated workload.                                     */
 int  zolo_refactor(zolo_factor_h h, void *stream);
@@ -212,6 +226,10 @@ int  zolo_apply(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y,
 
 /* ---- the eigensolver (Algorithm 1 with Algorithm 2 as the filter) ------- */
 /* Eigenpairs of (A, B) in (a, b) for an existing factor handle (its filter fixes the
+ * gaps).  When n_iter_max > 1 the first filter application, which starts from a random
+ * block, runs GMRES to max(gmres_tol, 1e-6) only: its output is filtered again by the
+ * next iteration; later applications use gmres_tol.  Results: see below.
+ *
  * gaps).  k0: subspace dimension (n_est estimate -> opts).  Results: evals[cap]
  * ascending (host), evecs n x cap device block (row-major, ld = ldv, B-orthonormal),
  * resid[cap] host residuals ||A x - lam B x||/(||A||_inf ||x||).  X0 (device, n x k0,
@@ -226,6 +244,16 @@ int  zolo_eigs(const zolo_csr *A, const zolo_csr *B, double a, double b, int64_t
                const zolo_filter_spec *spec, const zolo_opts *opts, double *evals, void *evecs,
                int64_t ldv, int64_t cap, int64_t *n_found, double *resid, zolo_stats *stats,
                void *stream);
+
+/* ---- measurement hooks (no counterpart in the paper) ---------------------- */
+/* Count the library's kernel launches from now on; gemm_events selects which dense-
+ * product (GEMM) launches are bracketed with CUDA events: bit 0 complex64, bit 1
+ * complex128 (0: none).  Process-wide, not thread-safe.                           */
+int  zolo_profile_begin(int32_t gemm_events);
+/* Synchronise `stream`, then report all launches, the timed GEMM launches, their summed
+ * device time (ms) and the flops those GEMM jobs executed (8 m n k each).           */
+int  zolo_profile_end(void *stream, int64_t *launches, int64_t *gemm_launches, double *gemm_ms,
+                      double *gemm_flops);
 
 #ifdef __cplusplus
 }

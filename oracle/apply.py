@@ -17,8 +17,13 @@ Three references, from the most to the least independent of the product:
 
 Readings (the paper leaves them open): zero initial guess, no restart, classical
 Gram-Schmidt applied twice, Euclidean inner product, one step count m for all
-columns of the block, stop at the first m where every shift's least-squares
-residual is <= tol * ||x_c|| for every column c, or at m_max.
+columns of the block.  Stop at the first m where, for every column c,
+    sum_s |omega_s| res_s / sqrt(l2^2 + |s|^2) <= tol * ||x_c||
+(res_s: least-squares residual of shift s), or at m_max.  The left side bounds the
+error of the filtered column: the combination's error is sum_s omega_s (G + s)^-1 r_s,
+G has real spectrum outside (-l2, l2) (|Zhat| >= l2 on the gap complement) and
+s = +-i sqrt(c) is imaginary, so ||(G + s)^-1|| <= 1 / sqrt(l2^2 + |s|^2) in the norm
+in which G is normal.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -93,9 +98,11 @@ def apply_hybrid(A, B, X, flt, tol=1e-12, m_max=100, G=None, return_info=False):
         m = i + 1
         worst = 0.0
         for c in range(k):
-            for s in shifts:
+            bound = 0.0
+            for s, om in zip(shifts, omegas):
                 _, res = _lsq(H[:m + 1, :m, c], s, beta[c])
-                worst = max(worst, res / beta[c])
+                bound += abs(om) * res / np.sqrt(flt.ell2 ** 2 + abs(s) ** 2)
+            worst = max(worst, bound / beta[c])
         if worst <= tol:
             break
     Y = 0.5 * X

@@ -6,7 +6,9 @@ Algorithm 1 (Section 2.1): Q orthonormal random; repeat { Y = R(B^-1 A) Q;
 A~ = Y^H A Y, B~ = Y^H B Y; solve A~ Q~ = Lam~ B~ Q~; Q = Y Q~ }; keep a < Lam~_ii < b.
 Readings: the generalized projected problem is solved through the B-Gram matrix
 B~ = U diag(mu) U^H, dropping directions with mu < drop * max(mu) (Y is nearly
-rank deficient after a sharp filter), then a standard Hermitian eigenproblem of
+rank deficient after a sharp filter; when the filtered block carries an error eps,
+drop must be at least ~(10 eps)^2 or noise directions survive), then a standard
+Hermitian eigenproblem of
 W^H A~ W with W = U_kept diag(mu^-1/2).  Selection is strict (a < lam < b),
 ascending; eigenvectors are B-normalised.
 

@@ -63,7 +63,7 @@ class Stats(C.Structure):
     _fields_ = [("n_iter", _i32), ("n_gmres", _i32), ("n_solv", _i64), ("n_refine_max", _i32),
                 ("n_found", _i32), ("gmres_res", _dbl), ("max_resid", _dbl), ("relerr", _dbl),
                 ("t_factor_ms", _dbl), ("t_apply_ms", _dbl), ("t_rr_ms", _dbl), ("t_total_ms", _dbl),
-                ("min_pivot", _dbl), ("flops_factor", _dbl), ("flops_solve", _dbl)]
+                ("min_pivot", _dbl), ("flops_factor", _dbl), ("flops_solve", _dbl), ("solve_cols", _i64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -100,6 +100,9 @@ _sig("zolo_symbolic_export", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp])
 _sig("zolo_symbolic_destroy", None, [_vp])
 _sig("zolo_factor", C.c_int, [_P(Csr), _P(Csr), _vp, _vp, _P(Opts), _vp, _P(_vp)])
 _sig("zolo_refactor", C.c_int, [_vp, _vp])
+_sig("zolo_inertia", C.c_int, [_P(Csr), _P(Csr), _vp, _P(Opts), _i32, _vp, _vp, _vp])
+_sig("zolo_profile_begin", C.c_int, [_i32])
+_sig("zolo_profile_end", C.c_int, [_vp, _P(_i64), _P(_i64), _P(_dbl), _P(_dbl)])
 _sig("zolo_factor_destroy", None, [_vp])
 _sig("zolo_factor_get_stats", C.c_int, [_vp, _P(Stats)])
 _sig("zolo_solve", C.c_int, [_vp, _i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp])
@@ -114,7 +117,7 @@ _sig("zolo_eigs", C.c_int, [_P(Csr), _P(Csr), _dbl, _dbl, _i64, _P(FilterSpec), 
 EXPORTED = ["zolo_opts_default", "zolo_strerror", "zolo_last_error", "zolo_version", "zolo_filter_build",
             "zolo_filter_get_info", "zolo_filter_eval", "zolo_filter_destroy", "zolo_analyze",
             "zolo_symbolic_get_info", "zolo_symbolic_export", "zolo_symbolic_destroy", "zolo_factor",
-            "zolo_refactor", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
+            "zolo_refactor", "zolo_inertia", "zolo_profile_begin", "zolo_profile_end", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
             "zolo_apply_inner", "zolo_apply", "zolo_eigs_factored", "zolo_eigs"]
 
 
@@ -215,6 +218,30 @@ class Symbolic:
         if getattr(self, "h", None):
             lib.zolo_symbolic_destroy(self.h)
             self.h = None
+
+
+def inertia(A, B, shifts, sym=None, opts=None, stream=None):
+    """Number of eigenvalues of (A, B) below each real shift (Sylvester's law of inertia)."""
+    hA, hB = HostCsr(A), HostCsr(B)
+    sh = np.ascontiguousarray(np.atleast_1d(np.asarray(shifts, dtype=np.float64)))
+    out = np.zeros(len(sh), dtype=np.int64)
+    o = opts if opts is not None else default_opts()
+    _check(lib.zolo_inertia(C.byref(hA.s), C.byref(hB.s), sym.h if sym is not None else None, C.byref(o),
+                            len(sh), sh.ctypes.data, out.ctypes.data, _stream(stream)), "zolo_inertia")
+    return out
+
+
+def profile_begin(gemm_events=0):
+    """Start counting the library's kernel launches (and time GEMM launches: 1 = complex64,
+    2 = complex128, 3 = both)."""
+    _check(lib.zolo_profile_begin(int(gemm_events)), "zolo_profile_begin")
+
+
+def profile_end(stream=None):
+    n, ng, ms, fl = _i64(0), _i64(0), _dbl(0), _dbl(0)
+    _check(lib.zolo_profile_end(_stream(stream), C.byref(n), C.byref(ng), C.byref(ms), C.byref(fl)),
+           "zolo_profile_end")
+    return {"launches": n.value, "gemm_launches": ng.value, "gemm_ms": ms.value, "gemm_flops": fl.value}
 
 
 def _stream(stream):

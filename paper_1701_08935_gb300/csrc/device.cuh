@@ -48,10 +48,11 @@ struct GJob {
     int32_t ars, acs, brs, bcs, crs, ccs;
     int32_t tile0;      // first tile of this job inside its launch
     int32_t tm;         // tiles along m
-    int32_t flags;      // GJ_CONJA | GJ_CONJB | GJ_SUB
-    int32_t pad;
+    int32_t flags;      // GJ_CONJA | GJ_CONJB | GJ_SUB | GJ_ACC
+    int32_t ks;         // split of the kk extent over ks CTAs (results added atomically)
 };
-enum { GJ_CONJA = 1, GJ_CONJB = 2, GJ_SUB = 4 };
+// GJ_SUB: C -= AB, GJ_ACC: C += AB, neither: C = AB (never split)
+enum { GJ_CONJA = 1, GJ_CONJB = 2, GJ_SUB = 4, GJ_ACC = 8 };
 
 // A diagonal block of a front: LU in place (FP64), inverses of L and U stored.
 struct DJob {

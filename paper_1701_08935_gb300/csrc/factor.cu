@@ -12,6 +12,7 @@
 // (U x = y, or L^H x = y) from the root, gathering the ancestors' solution rows.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include "factor.h"
 
@@ -77,20 +78,45 @@ GJob make_job(int64_t a, int ars, int acs, int64_t b, int brs, int bcs, int64_t 
     j.m = m; j.n = n; j.k = k;
     j.flags = flags;
     j.tm = (m + 63) / 64;
+    j.ks = 1;
     return j;
 }
 
-// append a launch of GEMM jobs (empty products dropped) and return its descriptor
-Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs) {
+// Precision of the launches being planned (complex64 launches may use 128-row tiles).
+thread_local bool g_plan_c64 = false;
+
+// Append a launch of GEMM jobs (empty products dropped) and return its descriptor.
+// Tile height: 128 rows for complex64 launches whose jobs average >= 256 rows, else 64.
+// With allow_split, a launch with fewer than ~4 waves of tiles splits the kk extent of its
+// accumulating jobs (GJ_SUB / GJ_ACC, kk >= 512) over several CTAs (atomic adds).
+Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs, bool allow_split = false) {
     Launch L;
     L.off = (int64_t)all.size();
+    double msum = 0.0;
+    int cnt = 0;
+    for (const GJob &j : jobs)
+        if (j.m > 0 && j.n > 0 && j.k > 0) {
+            msum += j.m;
+            ++cnt;
+        }
+    L.bm = (g_plan_c64 && cnt && msum / cnt >= 256.0) ? 128 : 64;
+    int base = 0;
+    for (const GJob &j : jobs)
+        if (j.m > 0 && j.n > 0 && j.k > 0) base += ((j.m + L.bm - 1) / L.bm) * ((j.n + 63) / 64);
+    const int target = 4 * 152;
+    const int factor = (allow_split && base > 0 && base < target) ? (target + base - 1) / base : 1;
     int tiles = 0;
     for (GJob j : jobs) {
         if (j.m <= 0 || j.n <= 0 || j.k <= 0) continue;
+        j.tm = (j.m + L.bm - 1) / L.bm;
+        j.ks = 1;
+        if (factor > 1 && (j.flags & (GJ_SUB | GJ_ACC)) && j.k >= 512)
+            j.ks = std::max(1, std::min({factor, j.k / 256, 16}));
         j.tile0 = tiles;
-        tiles += j.tm * ((j.n + 63) / 64);
+        tiles += j.tm * ((j.n + 63) / 64) * j.ks;
         all.push_back(j);
         L.cnt++;
+        L.flops += 8.0 * j.m * j.n * j.k;
     }
     L.ntiles = tiles;
     return L;
@@ -163,6 +189,13 @@ int upload_csr(zolo_factor_s *h, const zolo_csr *M, DevCSR &D) {
     int st = upload(h, rp, &D.rp);
     if (!st) st = upload(h, ci, &D.ci);
     if (!st) st = upload(h, v, &D.v);
+    bool real = true;
+    for (int64_t p = 0; p < M->nnz && real; ++p) real = (v[p].im == 0.0);
+    if (!st && real) {
+        std::vector<double> vr(M->nnz);
+        for (int64_t p = 0; p < M->nnz; ++p) vr[p] = v[p].re;
+        st = upload(h, vr, &D.vr);
+    }
     return st;
 }
 
@@ -171,13 +204,15 @@ size_t elem_bytes(int prec) { return prec == ZOLO_PREC_MIXED ? sizeof(c64) : siz
 // ---- layout, assembly maps and the factorisation schedule
 int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
     const zolo_symbolic_s &S = h->sym;
+    g_plan_c64 = (h->prec == ZOLO_PREC_MIXED);
     const int nn = S.nnodes;
     h->f_off.assign(nn, 0);
     h->f_inv.assign(nn, 0);
     h->f_wrow.assign(nn, 0);
     h->f_rows.assign(nn, 0);
     h->f_rel.assign(nn, -1);
-    int64_t po = 0, io = 0, wo = 0;
+    h->f_finv.assign(nn, 0);
+    int64_t po = 0, io = 0, wo = 0, fo = 0;
     std::vector<int32_t> rows;
     rows.reserve(S.n + S.urows.size());
     for (int idx = 0; idx < nn; ++idx) {
@@ -189,6 +224,8 @@ int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
         io += ((np + NB - 1) / NB) * 2 * NB * NB;
         h->f_wrow[s] = wo;
         wo += nf;
+        h->f_finv[s] = fo;
+        fo += 2 * np * np;
         h->f_rows[s] = (int64_t)rows.size();
         for (int64_t r = 0; r < np; ++r) rows.push_back(S.perm[S.first[s] + r]);
         for (int64_t p = S.uptr[s]; p < S.uptr[s + 1]; ++p) rows.push_back(S.perm[S.urows[p]]);
@@ -196,6 +233,7 @@ int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
     h->pool_elems = po;
     h->inv_elems = io;
     h->wrows = wo;
+    h->finv_elems = fo;
     // extend-add maps: child update row -> position in the parent front
     std::vector<int32_t> rel;
     for (int c = 0; c < nn; ++c) {
@@ -316,6 +354,54 @@ int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
             stp.schur = add_gemm(gj, sc);
             F.steps.push_back(stp);
         }
+        // explicit pivot-block inverses L_pp^-1 and U_pp^-1 (row-major np x np), computed by
+        // blocked substitution against the identity with the diagonal-block inverses
+        F.finv_lo = h->f_finv[s0];
+        F.finv_hi = h->f_finv[s1] + 2 * (int64_t)S.npiv[s1] * S.npiv[s1];
+        {
+            std::vector<RJob> ey;
+            for (int i = b; i < e; ++i) {
+                const int s = S.by_level[i];
+                ey.push_back(rjob(0, h->f_finv[s], 0, S.npiv[s]));
+            }
+            F.eye = add_rows(ej, ey, 256);
+        }
+        for (int t = 0; t * NB < maxnp; ++t) {                      // L: forward, rows below
+            std::vector<GJob> ap, up;
+            const int kb = t * NB;
+            for (int i = b; i < e; ++i) {
+                const int s = S.by_level[i];
+                const int np = S.npiv[s], nf = S.nf(s);
+                if (np <= kb) continue;
+                const int nb = std::min(NB, np - kb);
+                const int64_t X = h->f_finv[s], iv = h->f_inv[s] + (int64_t)t * 2 * NB * NB, o = h->f_off[s];
+                ap.push_back(make_job(iv, 1, NB, X + (int64_t)kb * np, np, 1, X + (int64_t)kb * np, np, 1, nb, kb + nb,
+                                      nb, 0));
+                up.push_back(make_job(o + kb + nb + (int64_t)kb * nf, 1, nf, X + (int64_t)kb * np, np, 1,
+                                      X + (int64_t)(kb + nb) * np, np, 1, np - kb - nb, kb + nb, nb, GJ_SUB));
+            }
+            F.linv.push_back(add_gemm(gj, ap));
+            F.linv.push_back(add_gemm(gj, up));
+        }
+        const int maxblk = (maxnp + NB - 1) / NB;
+        for (int t = 0; t < maxblk; ++t) {                           // U: backward, rows above
+            std::vector<GJob> ap, up;
+            for (int i = b; i < e; ++i) {
+                const int s = S.by_level[i];
+                const int np = S.npiv[s], nf = S.nf(s);
+                const int nblk = (np + NB - 1) / NB;
+                if (nblk <= t) continue;
+                const int bi = nblk - 1 - t, kb = bi * NB, nb = std::min(NB, np - kb);
+                const int64_t X = h->f_finv[s] + (int64_t)np * np;
+                const int64_t iv = h->f_inv[s] + (int64_t)bi * 2 * NB * NB + NB * NB, o = h->f_off[s];
+                ap.push_back(make_job(iv, 1, NB, X + (int64_t)kb * np + kb, np, 1, X + (int64_t)kb * np + kb, np, 1, nb,
+                                      np - kb, nb, 0));
+                up.push_back(make_job(o + (int64_t)kb * nf, 1, nf, X + (int64_t)kb * np + kb, np, 1, X + kb, np, 1, kb,
+                                      np - kb, nb, GJ_SUB));
+            }
+            F.uinv.push_back(add_gemm(gj, ap));
+            F.uinv.push_back(add_gemm(gj, up));
+        }
     }
     st = upload(h, dj, &h->d_djobs);
     if (!st) st = upload(h, gj, &h->d_fjobs);
@@ -330,15 +416,17 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
     const int np_ = h->r1;
     const size_t eb = sizeof(cx<T>);
     int rc = cuda_check(cudaMemsetAsync(h->d_err, 0, sizeof(int), st), "memset err");
+    if (!rc && h->count_neg) rc = cuda_check(cudaMemsetAsync(h->d_negcnt, 0, h->r1 * sizeof(int), st), "memset neg");
     if (rc) return rc;
     const int64_t *asrcA = h->d_asm, *adstA = h->d_asm + h->nA_asm;
     const int64_t *asrcB = h->d_asm + 2 * h->nA_asm, *adstB = asrcB + h->nB_asm;
     for (int p0 = 0; p0 < np_; p0 += MAX_INST) {
         const int ni = std::min(MAX_INST, np_ - p0);
-        cx<T> *pool[MAX_INST], *inv[MAX_INST];
+        cx<T> *pool[MAX_INST], *inv[MAX_INST], *finv[MAX_INST];
         for (int z = 0; z < ni; ++z) {
             pool[z] = (cx<T> *)h->pool[p0 + z];
             inv[z] = (cx<T> *)h->inv[p0 + z];
+            finv[z] = (cx<T> *)h->finv[p0 + z];
         }
         for (const FLevel &F : h->flev) {
             for (int z = 0; z < ni; ++z) {
@@ -378,6 +466,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                 da.njobs = S.diag.cnt;
                 da.err = h->d_err;
                 da.minpiv = h->d_minpiv + S.diag.off * np_ + (int64_t)p0 * S.diag.cnt;
+                da.negcnt = h->count_neg ? h->d_negcnt + p0 : nullptr;
                 for (int z = 0; z < ni; ++z) {
                     da.pool[z] = pool[z];
                     da.inv[z] = inv[z];
@@ -387,6 +476,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                     if (!L.cnt) return;
                     GemmArgs<T> g;
                     std::memset(&g, 0, sizeof(g));
+                    g.bm = L.bm;
                     for (int z = 0; z < ni; ++z) {
                         g.jobs[z] = h->d_fjobs + L.off;
                         g.njobs[z] = L.cnt;
@@ -395,11 +485,46 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                         g.B[z] = bbase ? inv[z] : pool[z];
                         g.C[z] = pool[z];
                     }
-                    launch_gemm<T>(g, ni, st);
+                    launch_gemm<T>(g, ni, st, L.flops * ni);
                 };
                 gemm(S.panelL, 0, 1);   // L21 = A21 Uinv
                 gemm(S.panelU, 1, 0);   // U12 = Linv A12
                 gemm(S.schur, 0, 0);    // A22 -= L21 U12
+            }
+            // pivot-block inverses of this level's fronts
+            for (int z = 0; z < ni; ++z) {
+                rc = cuda_check(cudaMemsetAsync(finv[z] + F.finv_lo, 0, (F.finv_hi - F.finv_lo) * eb, st), "memset inv");
+                if (rc) return rc;
+            }
+            EyeArgs<T> ey;
+            std::memset(&ey, 0, sizeof(ey));
+            ey.jobs = h->d_ejobs + F.eye.off;
+            ey.njobs = F.eye.cnt;
+            ey.ntiles = F.eye.ntiles;
+            for (int z = 0; z < ni; ++z) ey.P[z] = finv[z];
+            launch_eye<T>(ey, ni, st);
+            auto igemm = [&](const Launch &L, bool a_pool) {
+                if (!L.cnt) return;
+                GemmArgs<T> g;
+                std::memset(&g, 0, sizeof(g));
+                g.bm = L.bm;
+                for (int z = 0; z < ni; ++z) {
+                    g.jobs[z] = h->d_fjobs + L.off;
+                    g.njobs[z] = L.cnt;
+                    g.ntiles[z] = L.ntiles;
+                    g.A[z] = a_pool ? pool[z] : inv[z];
+                    g.B[z] = finv[z];
+                    g.C[z] = finv[z];
+                }
+                launch_gemm<T>(g, ni, st, L.flops * ni);
+            };
+            for (size_t q = 0; q + 1 < F.linv.size(); q += 2) {
+                igemm(F.linv[q], false);
+                igemm(F.linv[q + 1], true);
+            }
+            for (size_t q = 0; q + 1 < F.uinv.size(); q += 2) {
+                igemm(F.uinv[q], false);
+                igemm(F.uinv[q + 1], true);
             }
         }
     }
@@ -413,6 +538,8 @@ int factor_numeric(zolo_factor_s *h, cudaStream_t st) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
+    h->stats.solve_cols = 0;                       // per-factorisation counters
+    h->stats.n_refine_max = 0;
     int rc = (h->prec == ZOLO_PREC_MIXED) ? run_factor<float>(h, st) : run_factor<double>(h, st);
     cudaEventRecord(e1, st);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "factor");
@@ -439,20 +566,29 @@ int factor_numeric(zolo_factor_s *h, cudaStream_t st) {
 int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
     if (h->k_sched == k) return ZOLO_OK;
     const zolo_symbolic_s &S = h->sym;
+    g_plan_c64 = (h->prec == ZOLO_PREC_MIXED);
     std::vector<GJob> gj;
     std::vector<RJob> rj;
     h->fwd.clear();
     h->bwd.clear();
     const int K = (int)k;
     const int nl = S.nlevels;
-    auto gemm_op = [&](std::vector<GJob> &n, std::vector<GJob> &hh, int abase) {
+    auto gemm_op = [&](std::vector<GJob> &n, std::vector<GJob> &hh, int ab, int bb, int cb) {
         SOp o;
         o.kind = SOP_GEMM;
-        o.abase = abase;
-        o.L = add_gemm(gj, n);
-        o.LH = add_gemm(gj, hh);
+        o.abase = ab;
+        o.bbase = bb;
+        o.cbase = cb;
+        o.L = add_gemm(gj, n, true);
+        o.LH = add_gemm(gj, hh, true);
         return o;
     };
+    // Per front s (np pivots, nu update rows, W_s = its nf x k workspace rows, Y_s = its np
+    // rows of the pivot-row block, Linv/Uinv = explicit pivot-block inverses):
+    //   forward  K:   Y_s = Linv W_p,         W_u -= L_up Y_s         (children add W_u upwards)
+    //            K^H: Y_s = Uinv^H W_p,       W_u -= U_pu^H Y_s
+    //   backward K:   Y_s -= U_pu x_u,        x_p = Uinv Y_s
+    //            K^H: Y_s -= L_up^H x_u,      x_p = Linv^H Y_s
     for (int L = 0; L < nl; ++L) {                 // forward: leaves to root
         const int b = S.level_ptr[L], e = S.level_ptr[L + 1];
         std::vector<RJob> g;
@@ -480,75 +616,50 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
             oe.L = add_rows(rj, ea, ROWS_PER_TILE);
             h->fwd.push_back(oe);
         }
-        int maxnp = 0;
-        for (int i = b; i < e; ++i) maxnp = std::max(maxnp, S.npiv[S.by_level[i]]);
-        for (int t = 0; t * NB < maxnp; ++t) {
-            const int kb = t * NB;
-            std::vector<GJob> iN, iH, uN, uH;
-            for (int i = b; i < e; ++i) {
-                const int s = S.by_level[i];
-                const int np = S.npiv[s], nf = S.nf(s);
-                if (np <= kb) continue;
-                const int nb = std::min(NB, np - kb);
-                const int64_t iv = h->f_inv[s] + (int64_t)t * 2 * NB * NB, o = h->f_off[s];
-                const int64_t w = (h->f_wrow[s] + kb) * k;
-                iN.push_back(make_job(iv, 1, NB, w, K, 1, w, K, 1, nb, K, nb, 0));                      // Linv
-                iH.push_back(make_job(iv + NB * NB, NB, 1, w, K, 1, w, K, 1, nb, K, nb, GJ_CONJA));      // Uinv^H
-                const int rest = nf - kb - nb;
-                const int64_t wc = (h->f_wrow[s] + kb + nb) * k;
-                uN.push_back(make_job(o + kb + nb + (int64_t)kb * nf, 1, nf, w, K, 1, wc, K, 1, rest, K, nb, GJ_SUB));
-                uH.push_back(make_job(o + kb + (int64_t)(kb + nb) * nf, nf, 1, w, K, 1, wc, K, 1, rest, K, nb,
-                                      GJ_SUB | GJ_CONJA));
-            }
-            h->fwd.push_back(gemm_op(iN, iH, 1));
-            h->fwd.push_back(gemm_op(uN, uH, 0));
-        }
-    }
-    for (int L = nl - 1; L >= 0; --L) {           // backward: root to leaves
-        const int b = S.level_ptr[L], e = S.level_ptr[L + 1];
-        std::vector<RJob> g;
-        std::vector<GJob> aN, aH;
-        int maxblk = 0;
+        std::vector<GJob> yN, yH, uN, uH;
         for (int i = b; i < e; ++i) {
             const int s = S.by_level[i];
             const int np = S.npiv[s], nu = S.nu(s), nf = S.nf(s);
-            maxblk = std::max(maxblk, (np + NB - 1) / NB);
-            if (nu == 0) continue;
-            g.push_back(rjob(0, (h->f_wrow[s] + np) * k, h->f_rows[s] + np, nu));
-            const int64_t o = h->f_off[s];
-            const int64_t wu = (h->f_wrow[s] + np) * k, wp = h->f_wrow[s] * k;
-            aN.push_back(make_job(o + (int64_t)np * nf, 1, nf, wu, K, 1, wp, K, 1, np, K, nu, GJ_SUB));
-            aH.push_back(make_job(o + np, nf, 1, wu, K, 1, wp, K, 1, np, K, nu, GJ_SUB | GJ_CONJA));
+            const int64_t X = h->f_finv[s], o = h->f_off[s];
+            const int64_t wp = h->f_wrow[s] * k, wu = (h->f_wrow[s] + np) * k, y = (int64_t)S.first[s] * k;
+            // Y starts zeroed (the whole pivot-row block is cleared per solve): accumulate
+            yN.push_back(make_job(X, np, 1, wp, K, 1, y, K, 1, np, K, np, GJ_ACC));                     // Linv
+            yH.push_back(make_job(X + (int64_t)np * np, 1, np, wp, K, 1, y, K, 1, np, K, np,
+                                  GJ_ACC | GJ_CONJA));                                                   // Uinv^H
+            uN.push_back(make_job(o + np, 1, nf, y, K, 1, wu, K, 1, nu, K, np, GJ_SUB));                 // L_up
+            uH.push_back(make_job(o + (int64_t)np * nf, nf, 1, y, K, 1, wu, K, 1, nu, K, np, GJ_SUB | GJ_CONJA));
+        }
+        h->fwd.push_back(gemm_op(yN, yH, BK_INVFULL, BK_W, BK_YP));
+        h->fwd.push_back(gemm_op(uN, uH, BK_POOL, BK_YP, BK_W));
+    }
+    for (int L = nl - 1; L >= 0; --L) {           // backward: root to leaves
+        const int b = S.level_ptr[L], e = S.level_ptr[L + 1];
+        std::vector<RJob> g, sc, zr;
+        std::vector<GJob> aN, aH, xN, xH;
+        for (int i = b; i < e; ++i) {
+            const int s = S.by_level[i];
+            const int np = S.npiv[s], nu = S.nu(s), nf = S.nf(s);
+            const int64_t X = h->f_finv[s], o = h->f_off[s];
+            const int64_t wp = h->f_wrow[s] * k, wu = (h->f_wrow[s] + np) * k, y = (int64_t)S.first[s] * k;
+            if (nu > 0) g.push_back(rjob(0, wu, h->f_rows[s] + np, nu));
+            aN.push_back(make_job(o + (int64_t)np * nf, 1, nf, wu, K, 1, y, K, 1, np, K, nu, GJ_SUB));  // U_pu
+            aH.push_back(make_job(o + np, nf, 1, wu, K, 1, y, K, 1, np, K, nu, GJ_SUB | GJ_CONJA));      // L_up^H
+            // W_p is cleared first (ROW_ZERO), then accumulated into
+            xN.push_back(make_job(X + (int64_t)np * np, np, 1, y, K, 1, wp, K, 1, np, K, np, GJ_ACC));   // Uinv
+            xH.push_back(make_job(X, 1, np, y, K, 1, wp, K, 1, np, K, np, GJ_ACC | GJ_CONJA));           // Linv^H
+            sc.push_back(rjob(wp, 0, h->f_rows[s], np));
+            zr.push_back(rjob(0, wp, 0, np));
         }
         SOp og;
         og.kind = SOP_GATHER_OUT;
         og.L = add_rows(rj, g, ROWS_PER_TILE);
         h->bwd.push_back(og);
-        h->bwd.push_back(gemm_op(aN, aH, 0));
-        for (int t = 0; t < maxblk; ++t) {
-            std::vector<GJob> iN, iH, uN, uH;
-            for (int i = b; i < e; ++i) {
-                const int s = S.by_level[i];
-                const int np = S.npiv[s], nf = S.nf(s);
-                const int nblk = (np + NB - 1) / NB;
-                if (nblk <= t) continue;
-                const int bi = nblk - 1 - t;
-                const int kb = bi * NB, nb = std::min(NB, np - kb);
-                const int64_t iv = h->f_inv[s] + (int64_t)bi * 2 * NB * NB, o = h->f_off[s];
-                const int64_t w = (h->f_wrow[s] + kb) * k, w0 = h->f_wrow[s] * k;
-                iN.push_back(make_job(iv + NB * NB, 1, NB, w, K, 1, w, K, 1, nb, K, nb, 0));            // Uinv
-                iH.push_back(make_job(iv, NB, 1, w, K, 1, w, K, 1, nb, K, nb, GJ_CONJA));               // Linv^H
-                uN.push_back(make_job(o + (int64_t)kb * nf, 1, nf, w, K, 1, w0, K, 1, kb, K, nb, GJ_SUB));
-                uH.push_back(make_job(o + kb, nf, 1, w, K, 1, w0, K, 1, kb, K, nb, GJ_SUB | GJ_CONJA));
-            }
-            h->bwd.push_back(gemm_op(iN, iH, 1));
-            h->bwd.push_back(gemm_op(uN, uH, 0));
-        }
-        std::vector<RJob> sc;
-        for (int i = b; i < e; ++i) {
-            const int s = S.by_level[i];
-            sc.push_back(rjob(h->f_wrow[s] * k, 0, h->f_rows[s], S.npiv[s]));
-        }
+        h->bwd.push_back(gemm_op(aN, aH, BK_POOL, BK_W, BK_YP));
+        SOp oz;
+        oz.kind = SOP_ZERO;
+        oz.L = add_rows(rj, zr, ROWS_PER_TILE);
+        h->bwd.push_back(oz);
+        h->bwd.push_back(gemm_op(xN, xH, BK_INVFULL, BK_YP, BK_W));
         SOp os;
         os.kind = SOP_SCATTER_OUT;
         os.L = add_rows(rj, sc, ROWS_PER_TILE);
@@ -569,16 +680,21 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
     if (gb) rc = cuda_check(cudaMemcpy(h->d_sjobs, gj.data(), gb, cudaMemcpyHostToDevice), "sched");
     if (!rc && rb) rc = cuda_check(cudaMemcpy(h->d_rjobs, rj.data(), rb, cudaMemcpyHostToDevice), "sched");
     if (rc) return rc;
-    // workspaces
+    // workspaces: one front workspace and one pivot-row block per batched instance used
     if (h->w_buf.p) {
         dev_free(h, h->w_buf.p);
         h->w_buf = Buf();
     }
+    const int ninst = std::min(MAX_INST, 2 * h->r1);
     const size_t per = (size_t)h->wrows * k * elem_bytes(h->prec);
-    rc = dev_alloc(h, per * MAX_INST, &p);
+    const size_t pery = (size_t)h->n * k * elem_bytes(h->prec);
+    rc = dev_alloc(h, (per + pery) * ninst, &p);
     if (rc) return rc;
-    h->w_buf = Buf{p, per * MAX_INST};
-    for (int z = 0; z < MAX_INST; ++z) h->W[z] = (char *)p + z * per;
+    h->w_buf = Buf{p, (per + pery) * ninst};
+    for (int z = 0; z < MAX_INST; ++z) {
+        h->W[z] = z < ninst ? (char *)p + z * per : nullptr;
+        h->Yp[z] = z < ninst ? (char *)p + ninst * per + z * pery : nullptr;
+    }
     h->k_sched = k;
     return ZOLO_OK;
 }
@@ -589,8 +705,10 @@ template <class T>
 int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
               int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st) {
     const size_t per = (size_t)h->wrows * k * sizeof(cx<T>);
+    const size_t pery = (size_t)h->n * k * sizeof(cx<T>);
     for (int z = 0; z < ninst; ++z) {
         int rc = cuda_check(cudaMemsetAsync(h->W[z], 0, per, st), "memset W");
+        if (!rc) rc = cuda_check(cudaMemsetAsync(h->Yp[z], 0, pery, st), "memset Y");
         if (rc) return rc;
     }
     auto run = [&](const std::vector<SOp> &ops) {
@@ -598,16 +716,28 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
             if (o.kind == SOP_GEMM) {
                 GemmArgs<T> g;
                 std::memset(&g, 0, sizeof(g));
+                double fl = 0.0;
+                g.bm = o.L.bm;
+                auto base = [&](int kind, int z) -> cx<T> * {
+                    switch (kind) {
+                        case BK_POOL: return (cx<T> *)h->pool[pole[z]];
+                        case BK_INVBLK: return (cx<T> *)h->inv[pole[z]];
+                        case BK_INVFULL: return (cx<T> *)h->finv[pole[z]];
+                        case BK_YP: return (cx<T> *)h->Yp[z];
+                        default: return (cx<T> *)h->W[z];
+                    }
+                };
                 for (int z = 0; z < ninst; ++z) {
                     const Launch &L = herm[z] ? o.LH : o.L;
                     g.jobs[z] = h->d_sjobs + L.off;
                     g.njobs[z] = L.cnt;
                     g.ntiles[z] = L.ntiles;
-                    g.A[z] = (const cx<T> *)(o.abase ? h->inv[pole[z]] : h->pool[pole[z]]);
-                    g.B[z] = (const cx<T> *)h->W[z];
-                    g.C[z] = (cx<T> *)h->W[z];
+                    g.A[z] = base(o.abase, z);
+                    g.B[z] = base(o.bbase, z);
+                    g.C[z] = base(o.cbase, z);
+                    fl += L.flops;
                 }
-                launch_gemm<T>(g, ninst, st);
+                launch_gemm<T>(g, ninst, st, fl);
             } else {
                 RowArgs<T> r;
                 std::memset(&r, 0, sizeof(r));
@@ -617,7 +747,8 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                 r.map = (o.kind == SOP_EADD) ? h->d_rel : h->d_rows;
                 r.k = (int)k;
                 r.ldw = k;
-                r.mode = (o.kind == SOP_EADD) ? ROW_EADD : (o.kind == SOP_SCATTER_OUT ? ROW_SCATTER : ROW_GATHER);
+                r.mode = (o.kind == SOP_EADD) ? ROW_EADD
+                         : (o.kind == SOP_SCATTER_OUT ? ROW_SCATTER : (o.kind == SOP_ZERO ? ROW_ZERO : ROW_GATHER));
                 r.ldx = (o.kind == SOP_GATHER_IN) ? ldin : ldout;
                 for (int z = 0; z < ninst; ++z) {
                     r.W[z] = (cx<T> *)h->W[z];
@@ -636,9 +767,10 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
 
 int solve_batch(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
                 int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st) {
-    if (ninst > MAX_INST) return set_error(ZOLO_EINVAL, "internal: too many instances");
+    if (ninst > MAX_INST || ninst > 2 * h->r1) return set_error(ZOLO_EINVAL, "internal: too many instances");
     int rc = ensure_solve_schedule(h, k);
     if (rc) return rc;
+    h->stats.solve_cols += (int64_t)ninst * k;
     return (h->prec == ZOLO_PREC_MIXED) ? run_solve<float>(h, ninst, pole, herm, k, Xin, ldin, Xout, ldout, st)
                                         : run_solve<double>(h, ninst, pole, herm, k, Xin, ldin, Xout, ldout, st);
 }
@@ -696,29 +828,29 @@ int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, i
     const double tol = h->opts.refine_tol > 0 ? h->opts.refine_tol : 1e-13;
     const int itmax = h->opts.refine_max > 0 ? h->opts.refine_max : 8;
     for (int it = 0;; ++it) {
+        ResidArgs ra;
+        std::memset(&ra, 0, sizeof(ra));
+        ra.ninst = ninst;
+        ra.k = (int)k;
+        ra.ldb = ldin;
+        ra.ldx = ldout;
+        ra.ldr = k;
         for (int z = 0; z < ninst; ++z) {
-            LinArgs a;
-            std::memset(&a, 0, sizeof(a));
-            a.n = h->n;
-            a.k = k;
-            a.ldy = k;
-            a.Y = R + z * blk;
-            a.nterm = 1;
-            a.coef[0] = c128{1.0, 0.0};
-            a.X[0] = Xin[z];
-            a.ldx[0] = ldin;
-            launch_lincomb(a, st);
             const c128 sg{h->fi.sigma_hat[2 * pole[z]], h->fi.sigma_hat[2 * pole[z] + 1]};
-            launch_spmm(h->A, k, Xout[z], ldout, R + z * blk, k, c128{-1.0, 0.0}, true, st);
-            launch_spmm(h->B, k, Xout[z], ldout, R + z * blk, k, herm[z] ? conj(sg) : sg, true, st);
-            launch_colnorm2(h->n, k, R + z * blk, k, h->d_norms + z * k, st);
+            ra.Bz[z] = Xin[z];
+            ra.Xz[z] = Xout[z];
+            ra.Rz[z] = R + z * blk;
+            ra.s[z] = herm[z] ? conj(sg) : sg;          // K^H = A - conj(sigma) B
         }
+        launch_refine_resid(h->A, h->B, ra, st);
+        for (int z = 0; z < ninst; ++z) launch_colnorm2(h->n, k, R + z * blk, k, h->d_norms + z * k, st);
         rc = cuda_check(cudaMemcpyAsync(hr.data(), h->d_norms, ninst * k * sizeof(double), cudaMemcpyDeviceToHost, st),
                         "norms");
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "norms");
         if (rc) return rc;
         double worst = 0.0;
         for (int64_t i = 0; i < ninst * k; ++i) worst = std::max(worst, std::sqrt(hr[i] / std::max(hb[i], 1e-300)));
+        if (h->opts.verbose) std::fprintf(stderr, "[zolo] refine step %d: max ||b - K x|| / ||b|| = %.3e\n", it, worst);
         if (worst <= tol) break;
         if (it >= itmax) return set_error(ZOLO_ENOCONV, "refinement of a shifted solve did not converge (" +
                                                             std::to_string(worst) + ")");
@@ -756,7 +888,7 @@ int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
     const int r1 = h->r1;
     const int nblk = 1 + 2 * r1;
     c128 *scr = nullptr;
-    int rc = ensure_scratch(h, k, nblk + 2 * std::min(2 * r1, MAX_INST), &scr);
+    int rc = ensure_scratch(h, k, nblk, &scr);
     if (rc) return rc;
     c128 *BX = scr;
     launch_spmm(h->B, k, X, ldx, BX, k, c128{1.0, 0.0}, false, st);
@@ -814,10 +946,12 @@ using namespace zolo;
 
 extern "C" {
 
-int zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbolic sym, const zolo_opts *opts,
-                void *stream, zolo_factor_h *out) {
-    clear_error();
-    if (!out || !f) return set_error(ZOLO_EINVAL, "null argument");
+}  // extern "C"
+
+namespace zolo {
+// Upload the pencil and factor A - sigma_j B for the given poles (sigma as re, im pairs).
+static int factor_create(const zolo_csr *A, const zolo_csr *B, const zolo_filter_info &fi, zolo_symbolic sym,
+                         const zolo_opts *opts, cudaStream_t stream, bool count_neg, zolo_factor_s **out) {
     *out = nullptr;
     bool ca, cb;
     int rc = check_csr(A, "A", ca);
@@ -829,8 +963,9 @@ int zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbol
     h->prec = h->opts.precision == ZOLO_PREC_MIXED ? ZOLO_PREC_MIXED : ZOLO_PREC_FP64;
     h->n = A->n;
     h->cplx = ca || cb;
-    h->fi = f->info;
-    h->r1 = f->info.r1;
+    h->fi = fi;
+    h->r1 = fi.r1;
+    h->count_neg = count_neg;
     std::memset(&h->stats, 0, sizeof(h->stats));
     cudaGetDevice(&h->device);
     double nb_inf = 0.0;
@@ -856,20 +991,93 @@ int zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbol
     rc = upload_csr(h, A, h->A);
     if (!rc) rc = upload_csr(h, B, h->B);
     if (!rc) rc = build_factor_plan(h, A, B);
+    if (!rc && count_neg) rc = dev_alloc(h, h->r1 * sizeof(int), (void **)&h->d_negcnt);
     const size_t eb = elem_bytes(h->prec);
     for (int j = 0; !rc && j < h->r1; ++j) {
         rc = dev_alloc(h, h->pool_elems * eb, &h->pool[j]);
         if (!rc) rc = dev_alloc(h, std::max<int64_t>(1, h->inv_elems) * eb, &h->inv[j]);
+        if (!rc) rc = dev_alloc(h, std::max<int64_t>(1, h->finv_elems) * eb, &h->finv[j]);
     }
     h->stats.flops_factor = h->sym.info.flops_lu * h->r1;
     h->stats.flops_solve = 16.0 * (double)h->sym.info.nnz_factor;     // fwd + bwd, complex, per column
-    if (!rc) rc = factor_numeric(h, (cudaStream_t)stream);
+    if (!rc) rc = factor_numeric(h, stream);
     if (rc) {
         zolo_factor_destroy(h);
         return rc;
     }
     *out = h;
     return ZOLO_OK;
+}
+}  // namespace zolo
+
+extern "C" {
+
+int zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbolic sym, const zolo_opts *opts,
+                void *stream, zolo_factor_h *out) {
+    clear_error();
+    if (!out || !f) return set_error(ZOLO_EINVAL, "null argument");
+    return factor_create(A, B, f->info, sym, opts, (cudaStream_t)stream, false, out);
+}
+
+int zolo_inertia(const zolo_csr *A, const zolo_csr *B, zolo_symbolic sym, const zolo_opts *opts, int32_t nshift,
+                 const double *sigma, int64_t *count, void *stream) {
+    clear_error();
+    if (!sigma || !count || nshift < 1) return set_error(ZOLO_EINVAL, "bad argument");
+    for (int i = 0; i < nshift; ++i)
+        if (!std::isfinite(sigma[i])) return set_error(ZOLO_EINVAL, "non-finite shift");
+    // Always complex128 fronts: the no-pivot LDL^H of an indefinite A - sigma B keeps the
+    // signs of its pivots only with FP64 arithmetic (complex64 counts are unreliable).
+    zolo_opts o;
+    if (opts) o = *opts; else zolo_opts_default(&o);
+    o.precision = ZOLO_PREC_FP64;
+    zolo_symbolic_s local;
+    const zolo_symbolic_s *S = sym;
+    if (!S) {
+        int rc = analyze(A, B, o, local);
+        if (rc) return rc;
+        S = &local;
+    }
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const double per_shift = (double)S->info.front_entries * sizeof(c128);
+    int batch = (int)std::max(1.0, std::min((double)std::min(nshift, ZOLO_MAX_R),
+                                             0.45 * (double)fr / std::max(per_shift, 1.0)));
+    for (int i0 = 0; i0 < nshift; i0 += batch) {
+        const int nb = std::min(batch, nshift - i0);
+        zolo_filter_info fi;
+        std::memset(&fi, 0, sizeof(fi));
+        fi.r1 = nb;
+        for (int i = 0; i < nb; ++i) fi.sigma_hat[2 * i] = sigma[i0 + i];
+        zolo_factor_s *h = nullptr;
+        int rc = factor_create(A, B, fi, const_cast<zolo_symbolic_s *>(S), &o, (cudaStream_t)stream, true, &h);
+        if (rc) return rc;
+        std::vector<int> neg(nb);
+        rc = cuda_check(cudaMemcpy(neg.data(), h->d_negcnt, nb * sizeof(int), cudaMemcpyDeviceToHost), "inertia");
+        for (int i = 0; i < nb && !rc; ++i) count[i0 + i] = neg[i];
+        zolo_factor_destroy(h);
+        if (rc) return rc;
+    }
+    return ZOLO_OK;
+}
+
+int zolo_profile_begin(int32_t gemm_events) {
+    clear_error();
+    prof_collect_ms();
+    counters() = LaunchCounters();
+    prof_set(gemm_events);
+    return ZOLO_OK;
+}
+
+int zolo_profile_end(void *stream, int64_t *launches, int64_t *gemm_launches, double *gemm_ms, double *gemm_flops) {
+    clear_error();
+    int rc = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "profile");
+    const double ms = prof_collect_ms();
+    prof_set(0);
+    if (launches) *launches = counters().launches;
+    if (gemm_launches) *gemm_launches = counters().gemm_launches;
+    if (gemm_ms) *gemm_ms = ms;
+    if (gemm_flops) *gemm_flops = counters().gemm_flops;
+    return rc;
 }
 
 int zolo_refactor(zolo_factor_h h, void *stream) {

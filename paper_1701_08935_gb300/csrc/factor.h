@@ -11,6 +11,8 @@ struct Launch {
     int64_t off = 0;     // first job in the device job array
     int cnt = 0;         // jobs
     int ntiles = 0;      // CTAs
+    double flops = 0.0;  // executed flops of a GEMM launch (8 m n k summed over jobs)
+    int bm = 64;         // GEMM tile height of the launch
 };
 
 // one step of a level's factorisation: diagonal blocks, the two panels, Schur update
@@ -20,19 +22,25 @@ struct FStep {
 
 struct FLevel {
     int64_t pool_lo = 0, pool_hi = 0;              // the level's fronts are contiguous
+    int64_t finv_lo = 0, finv_hi = 0;              // ... and so are their pivot-block inverses
+    Launch eye;                                     // identity start of those inverses
+    std::vector<Launch> linv, uinv;                // (apply, update) pairs per panel step
     int64_t asmA_lo = 0, asmA_hi = 0, asmB_lo = 0, asmB_hi = 0;
     std::vector<Launch> eadd;                      // one per child slot
     std::vector<FStep> steps;
 };
 
+// operand bases of a GEMM launch
+enum { BK_POOL = 0, BK_INVBLK = 1, BK_INVFULL = 2, BK_W = 3, BK_YP = 4 };
+
 // one launch of the block solve: rows kernel or GEMM
 struct SOp {
     int kind = 0;        // SOP_*
-    int abase = 0;       // GEMM: A operand in the front pool (0) or the inverse store (1)
+    int abase = 0, bbase = BK_W, cbase = BK_W;      // GEMM operand bases (BK_*)
     Launch L;            // rows jobs, or GEMM jobs for K^-1
     Launch LH;           // GEMM jobs for K^-H
 };
-enum { SOP_GATHER_IN = 0, SOP_EADD = 1, SOP_GEMM = 2, SOP_GATHER_OUT = 3, SOP_SCATTER_OUT = 4 };
+enum { SOP_GATHER_IN = 0, SOP_EADD = 1, SOP_GEMM = 2, SOP_GATHER_OUT = 3, SOP_SCATTER_OUT = 4, SOP_ZERO = 5 };
 
 struct Buf {
     void *p = nullptr;
@@ -57,10 +65,12 @@ struct zolo_factor_s {
     std::vector<zolo::Buf> owned;                  // every device allocation
 
     // front layout (per node)
-    std::vector<int64_t> f_off, f_inv, f_wrow, f_rows, f_rel;
-    int64_t pool_elems = 0, inv_elems = 0, wrows = 0;
+    std::vector<int64_t> f_off, f_inv, f_wrow, f_rows, f_rel, f_finv;
+    int64_t pool_elems = 0, inv_elems = 0, wrows = 0, finv_elems = 0;
     void *pool[ZOLO_MAX_R] = {};                   // per pole: fronts (T)
     void *inv[ZOLO_MAX_R] = {};                    // per pole: diagonal-block inverses (T)
+    void *finv[ZOLO_MAX_R] = {};                   // per pole: full pivot-block inverses, L then U
+                                                   // (np x np each, row-major)
     int32_t *d_rows = nullptr, *d_rel = nullptr;
     int64_t *d_asm = nullptr;                      // [srcA | dstA | srcB | dstB]
     int64_t nA_asm = 0, nB_asm = 0;
@@ -81,6 +91,7 @@ struct zolo_factor_s {
     zolo::RJob *d_rjobs = nullptr;
     zolo::Buf sched_buf;
     void *W[zolo::MAX_INST] = {};                  // front workspaces (T), wrows x k each
+    void *Yp[zolo::MAX_INST] = {};                 // pivot-row intermediates (T), n x k each
     zolo::Buf w_buf;
 
     // scratch for the inner operator and for refinement (complex128, n x k blocks)
@@ -89,6 +100,9 @@ struct zolo_factor_s {
     int64_t norms_k = 0;
 
     zolo::KrylovWork *kw = nullptr;
+    double gmres_tol_now = 0.0;                    // tolerance of the current filter application
+    int *d_negcnt = nullptr;                       // inertia: negative pivots per pole
+    bool count_neg = false;
     zolo_stats stats;
 };
 

@@ -5,7 +5,42 @@
 // all fronts of one tree level, so one launch covers a whole level.
 #include "kernels.cuh"
 
+#include <vector>
+
 namespace zolo {
+
+namespace {
+LaunchCounters g_counters;
+int g_prof = 0;                      // bit 0: time complex64 GEMMs, bit 1: complex128
+std::vector<cudaEvent_t> g_ev;       // start/stop pairs of profiled GEMM launches
+std::vector<cudaEvent_t> g_ev_pool;
+cudaEvent_t get_event() {
+    if (!g_ev_pool.empty()) {
+        cudaEvent_t e = g_ev_pool.back();
+        g_ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+LaunchCounters &counters() { return g_counters; }
+void count_launch(int64_t n) { g_counters.launches += n; }
+void prof_set(int mask) { g_prof = mask; }
+double prof_collect_ms() {
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < g_ev.size(); i += 2) {
+        cudaEventSynchronize(g_ev[i + 1]);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, g_ev[i], g_ev[i + 1]);
+        ms += t;
+    }
+    for (cudaEvent_t e : g_ev) g_ev_pool.push_back(e);
+    g_ev.clear();
+    return ms;
+}
 
 // ============================================================== batched GEMM
 // C (=|-=) op(A) op(B) for every job in the list; one CTA per BM x BN tile.
@@ -31,8 +66,14 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
     }
     __syncthreads();
     const GJob J = jobs[s_job];
-    const int t = tile - J.tile0;
+    int t = tile - J.tile0;
+    const int tmn = J.tm * ((J.n + BN - 1) / BN);
+    const int kslice = t / tmn;
+    t -= kslice * tmn;
     const int i0 = (t % J.tm) * BM, j0 = (t / J.tm) * BN;
+    const int ksp = J.ks > 1 ? J.ks : 1;
+    const int kchunk = (((J.k + ksp - 1) / ksp) + BK - 1) / BK * BK;
+    const int kbeg = kslice * kchunk, kend = min(J.k, kbeg + kchunk);
     const cx<T> *__restrict__ A = g.A[z] + J.a;
     const cx<T> *__restrict__ B = g.B[z] + J.b;
     const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
@@ -43,7 +84,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = mk<T>(0, 0);
 
-    for (int l0 = 0; l0 < J.k; l0 += BK) {
+    for (int l0 = kbeg; l0 < kend; l0 += BK) {
         // ---- stage A tile (BM x BK) and B tile (BK x BN)
 #pragma unroll
         for (int q = 0; q < (BM * BK) / 256; ++q) {
@@ -51,7 +92,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
             int i, l;
             if (J.ars == 1) { i = e % BM; l = e / BM; } else { l = e % BK; i = e / BK; }
             cx<T> v = mk<T>(0, 0);
-            if (i0 + i < J.m && l0 + l < J.k) v = A[(int64_t)(i0 + i) * J.ars + (int64_t)(l0 + l) * J.acs];
+            if (i0 + i < J.m && l0 + l < kend) v = A[(int64_t)(i0 + i) * J.ars + (int64_t)(l0 + l) * J.acs];
             As[l][i] = conjA ? conj(v) : v;
         }
 #pragma unroll
@@ -60,7 +101,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
             int j, l;
             if (J.brs == 1) { l = e % BK; j = e / BK; } else { j = e % BN; l = e / BN; }
             cx<T> v = mk<T>(0, 0);
-            if (j0 + j < J.n && l0 + l < J.k) v = B[(int64_t)(l0 + l) * J.brs + (int64_t)(j0 + j) * J.bcs];
+            if (j0 + j < J.n && l0 + l < kend) v = B[(int64_t)(l0 + l) * J.brs + (int64_t)(j0 + j) * J.bcs];
             Bs[l][j] = conjB ? conj(v) : v;
         }
         __syncthreads();
@@ -79,7 +120,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
         __syncthreads();
     }
     cx<T> *__restrict__ C = g.C[z] + J.c;
-    const bool sub = J.flags & GJ_SUB;
+    const bool sub = J.flags & GJ_SUB, add = J.flags & GJ_ACC, atom = J.ks > 1;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int i = i0 + ty + 16 * r;
@@ -89,18 +130,178 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
             const int j = j0 + tx + 16 * c;
             if (j >= J.n) continue;
             cx<T> *p = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
-            *p = sub ? (*p - acc[r][c]) : acc[r][c];
+            const cx<T> v = sub ? mk<T>(-acc[r][c].re, -acc[r][c].im) : acc[r][c];
+            if (atom) {
+                atomicAdd(&p->re, v.re);
+                atomicAdd(&p->im, v.im);
+            } else {
+                *p = (sub || add) ? (*p + v) : v;
+            }
+        }
+    }
+}
+
+// Complex64 variant for the FP32 pipe: 128 x 64 C tile per CTA, each thread an 8 x 4 block of
+// complex outputs (rows ty*4 + {0..3} and 64 + ty*4 + {0..3}, columns tx*2 + {0,1} and
+// 32 + tx*2 + {0,1}) fed by 128-bit shared-memory reads; the next k-tile is prefetched into
+// registers while the current one is consumed.  Same job semantics (and in-place rules)
+// as k_gemm, with tiles of GEMM_BM_C64 rows.
+constexpr int G2_BM = 128, G2_BN = 64, G2_BK = 16;
+__global__ void __launch_bounds__(256) k_gemm_c64(GemmArgs<float> g) {
+    const int z = blockIdx.z;
+    const int tile = blockIdx.x;
+    if (tile >= g.ntiles[z]) return;
+    const GJob *jobs = g.jobs[z];
+    __shared__ int s_job;
+    __shared__ __align__(16) c64 As[G2_BK][G2_BM];
+    __shared__ __align__(16) c64 Bs[G2_BK][G2_BN];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int lo = 0, hi = g.njobs[z] - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const GJob J = jobs[s_job];
+    int t = tile - J.tile0;
+    const int tmn = J.tm * ((J.n + G2_BN - 1) / G2_BN);
+    const int kslice = t / tmn;
+    t -= kslice * tmn;
+    const int i0 = (t % J.tm) * G2_BM, j0 = (t / J.tm) * G2_BN;
+    const int ksp = J.ks > 1 ? J.ks : 1;
+    const int kchunk = (((J.k + ksp - 1) / ksp) + G2_BK - 1) / G2_BK * G2_BK;
+    const int kbeg = kslice * kchunk, kend = min(J.k, kbeg + kchunk);
+    const c64 *__restrict__ A = g.A[z] + J.a;
+    const c64 *__restrict__ B = g.B[z] + J.b;
+    const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
+    const bool a_rowfast = (J.ars == 1), b_rowfast = (J.brs == 1);
+    const int tx = tid & 15, ty = tid >> 4;
+    float acc[8][4][2];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c][0] = acc[r][c][1] = 0.f;
+    c64 ra[8], rb[4];
+    auto load = [&](int l0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = tid + 256 * q;
+            int i, l;
+            if (a_rowfast) { i = e % G2_BM; l = e / G2_BM; } else { l = e % G2_BK; i = e / G2_BK; }
+            c64 v = mk<float>(0, 0);
+            if (i0 + i < J.m && l0 + l < kend) v = A[(int64_t)(i0 + i) * J.ars + (int64_t)(l0 + l) * J.acs];
+            ra[q] = conjA ? conj(v) : v;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            int j, l;
+            if (b_rowfast) { l = e % G2_BK; j = e / G2_BK; } else { j = e % G2_BN; l = e / G2_BN; }
+            c64 v = mk<float>(0, 0);
+            if (j0 + j < J.n && l0 + l < kend) v = B[(int64_t)(l0 + l) * J.brs + (int64_t)(j0 + j) * J.bcs];
+            rb[q] = conjB ? conj(v) : v;
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = tid + 256 * q;
+            int i, l;
+            if (a_rowfast) { i = e % G2_BM; l = e / G2_BM; } else { l = e % G2_BK; i = e / G2_BK; }
+            As[l][i] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            int j, l;
+            if (b_rowfast) { l = e % G2_BK; j = e / G2_BK; } else { j = e % G2_BN; l = e / G2_BN; }
+            Bs[l][j] = rb[q];
+        }
+    };
+    load(kbeg);
+    for (int l0 = kbeg; l0 < kend; l0 += G2_BK) {
+        __syncthreads();
+        store();
+        __syncthreads();
+        if (l0 + G2_BK < kend) load(l0 + G2_BK);
+#pragma unroll 4
+        for (int l = 0; l < G2_BK; ++l) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[l][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[l][ty * 4 + 2]);
+            const float4 a2 = *reinterpret_cast<const float4 *>(&As[l][64 + ty * 4]);
+            const float4 a3 = *reinterpret_cast<const float4 *>(&As[l][64 + ty * 4 + 2]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[l][tx * 2]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[l][32 + tx * 2]);
+            const float ar[8] = {a0.x, a0.z, a1.x, a1.z, a2.x, a2.z, a3.x, a3.z};
+            const float ai[8] = {a0.y, a0.w, a1.y, a1.w, a2.y, a2.w, a3.y, a3.w};
+            const float br[4] = {b0.x, b0.z, b1.x, b1.z};
+            const float bi[4] = {b0.y, b0.w, b1.y, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    acc[r][c][0] = fmaf(ar[r], br[c], acc[r][c][0]);
+                    acc[r][c][0] = fmaf(-ai[r], bi[c], acc[r][c][0]);
+                    acc[r][c][1] = fmaf(ar[r], bi[c], acc[r][c][1]);
+                    acc[r][c][1] = fmaf(ai[r], br[c], acc[r][c][1]);
+                }
+        }
+    }
+    c64 *__restrict__ C = g.C[z] + J.c;
+    const bool sub = J.flags & GJ_SUB, add = J.flags & GJ_ACC, atom = J.ks > 1;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+        if (i >= J.m) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = j0 + (c < 2 ? tx * 2 + c : 32 + tx * 2 + (c - 2));
+            if (j >= J.n) continue;
+            c64 *p = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
+            const c64 v = sub ? mk<float>(-acc[r][c][0], -acc[r][c][1]) : mk<float>(acc[r][c][0], acc[r][c][1]);
+            if (atom) {
+                atomicAdd(reinterpret_cast<float2 *>(p), make_float2(v.re, v.im));
+            } else {
+                *p = (sub || add) ? (*p + v) : v;
+            }
         }
     }
 }
 
 template <class T>
-void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st) {
+void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops) {
     int mx = 0;
     for (int z = 0; z < ninst; ++z) mx = g.ntiles[z] > mx ? g.ntiles[z] : mx;
     if (mx == 0) return;
     dim3 grid(mx, 1, ninst);
-    k_gemm<T, 64, 64, 16><<<grid, 256, 0, st>>>(g);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = (g_prof & (sizeof(T) == 4 ? 1 : 2)) != 0;
+    if (timed) {
+        e0 = get_event();
+        e1 = get_event();
+        cudaEventRecord(e0, st);
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (g.bm == G2_BM)
+            k_gemm_c64<<<grid, 256, 0, st>>>(g);
+        else
+            k_gemm<T, 64, 64, 16><<<grid, 256, 0, st>>>(g);
+    } else {
+        k_gemm<T, 64, 64, 16><<<grid, 256, 0, st>>>(g);
+    }
+    if (timed) {
+        cudaEventRecord(e1, st);
+        g_ev.push_back(e0);
+        g_ev.push_back(e1);
+    }
+    g_counters.launches++;
+    if (timed) {
+        g_counters.gemm_launches++;
+        g_counters.gemm_flops += flops;
+    }
 }
 
 // ============================================================== diagonal blocks
@@ -123,11 +324,13 @@ __global__ void __launch_bounds__(256) k_diag_lu(DiagArgs<T> g) {
     }
     __syncthreads();
     double minpiv = 1e300;
+    int neg = 0;
     for (int p = 0; p < nb; ++p) {
         const c128 piv = blk[p + p * NB];
         const double a2 = abs2(piv);
         if (tid == 0) {
             minpiv = fmin(minpiv, sqrt(a2));
+            neg += piv.re < 0.0 ? 1 : 0;
             if (!(a2 > 0.0) || !isfinite(a2)) atomicOr(g.err, 1);
         }
         const c128 ip = (a2 > 0.0 && isfinite(a2)) ? cdiv(mk<double>(1, 0), piv) : mk<double>(0, 0);
@@ -140,7 +343,10 @@ __global__ void __launch_bounds__(256) k_diag_lu(DiagArgs<T> g) {
         }
         __syncthreads();
     }
-    if (tid == 0) g.minpiv[(int64_t)z * g.njobs + blockIdx.x] = minpiv;
+    if (tid == 0) {
+        g.minpiv[(int64_t)z * g.njobs + blockIdx.x] = minpiv;
+        if (g.negcnt) atomicAdd(g.negcnt + z, neg);
+    }
     cx<T> *Li = g.inv[z] + J.inv;
     cx<T> *Ui = Li + NB * NB;
     // Linv: column j solves L x = e_j (unit lower)
@@ -188,6 +394,7 @@ void launch_diag_lu(const DiagArgs<T> &g, int ninst, cudaStream_t st) {
     }
     dim3 grid(g.njobs, 1, ninst);
     k_diag_lu<T><<<grid, 256, smem, st>>>(g);
+    g_counters.launches++;
 }
 
 // ============================================================== assembly
@@ -208,6 +415,7 @@ void launch_assemble(const AsmArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.count == 0) return;
     dim3 grid((unsigned)((g.count + 255) / 256), 1, ninst);
     k_assemble<T><<<grid, 256, 0, st>>>(g);
+    g_counters.launches++;
 }
 
 // ============================================================== matrix extend-add
@@ -250,6 +458,7 @@ void launch_extend_add(const EaddArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.ntiles == 0) return;
     dim3 grid(g.ntiles, 1, ninst);
     k_extend_add<T><<<grid, 256, 0, st>>>(g);
+    g_counters.launches++;
 }
 
 // ============================================================== row moves
@@ -285,6 +494,8 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> g) {
             W[J.dst + (int64_t)r * g.ldw + c] = cvt<T>(X[(int64_t)map[r] * g.ldx + c]);
         } else if (g.mode == ROW_SCATTER) {
             X[(int64_t)map[r] * g.ldx + c] = cvt<double>(W[J.src + (int64_t)r * g.ldw + c]);
+        } else if (g.mode == ROW_ZERO) {
+            W[J.dst + (int64_t)r * g.ldw + c] = mk<T>(0, 0);
         } else {
             cx<T> *p = W + J.dst + (int64_t)map[r] * g.ldw + c;
             *p = *p + W[J.src + (int64_t)r * g.ldw + c];
@@ -297,6 +508,39 @@ void launch_rows(const RowArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.ntiles == 0) return;
     dim3 grid(g.ntiles, 1, ninst);
     k_rows<T><<<grid, 256, 0, st>>>(g);
+    g_counters.launches++;
+}
+
+// ============================================================== identity starts
+template <class T>
+__global__ void __launch_bounds__(256) k_eye_blocks(EyeArgs<T> g) {
+    const int z = blockIdx.z;
+    const int tile = blockIdx.x;
+    if (tile >= g.ntiles) return;
+    __shared__ int s_job;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = g.njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const RJob J = g.jobs[s_job];
+    const int i = (tile - J.tile0) * 256 + threadIdx.x;
+    if (i >= J.rows) return;
+    const int64_t r = J.rows;
+    g.P[z][J.dst + i * (r + 1)] = mk<T>(1, 0);
+    g.P[z][J.dst + r * r + i * (r + 1)] = mk<T>(1, 0);
+}
+
+template <class T>
+void launch_eye(const EyeArgs<T> &g, int ninst, cudaStream_t st) {
+    if (g.ntiles == 0) return;
+    dim3 grid(g.ntiles, 1, ninst);
+    k_eye_blocks<T><<<grid, 256, 0, st>>>(g);
+    g_counters.launches++;
 }
 
 // ============================================================== SpMM
@@ -319,11 +563,73 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t *__restrict__ rp, co
     }
 }
 
+// real-valued matrix (e.g. a mass matrix): 2 real FMAs per entry instead of 4
+__global__ void __launch_bounds__(256) k_spmm_real(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                   const double *__restrict__ v, int64_t n, int k,
+                                                   const c128 *__restrict__ X, int64_t ldx, c128 *__restrict__ Y,
+                                                   int64_t ldy, c128 s, int acc) {
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = rp[row], e = rp[row + 1];
+    for (int c = lane; c < k; c += 32) {
+        double sr = 0.0, si = 0.0;
+        for (int64_t p = b; p < e; ++p) {
+            const double a = v[p];
+            const c128 x = X[(int64_t)ci[p] * ldx + c];
+            sr = fma(a, x.re, sr);
+            si = fma(a, x.im, si);
+        }
+        c128 *y = Y + row * ldy + c;
+        const c128 t = s * mk<double>(sr, si);
+        *y = acc ? (*y + t) : t;
+    }
+}
+
 void launch_spmm(const DevCSR &M, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, c128 s,
                  bool acc, cudaStream_t st) {
     if (M.n == 0 || k == 0) return;
     dim3 grid((unsigned)((M.n + 7) / 8));
-    k_spmm<<<grid, 256, 0, st>>>(M.rp, M.ci, M.v, M.n, (int)k, X, ldx, Y, ldy, s, acc ? 1 : 0);
+    if (M.vr)
+        k_spmm_real<<<grid, 256, 0, st>>>(M.rp, M.ci, M.vr, M.n, (int)k, X, ldx, Y, ldy, s, acc ? 1 : 0);
+    else
+        k_spmm<<<grid, 256, 0, st>>>(M.rp, M.ci, M.v, M.n, (int)k, X, ldx, Y, ldy, s, acc ? 1 : 0);
+    g_counters.launches++;
+}
+
+// Refinement residuals of all instances in one pass over the rows of A and M
+__global__ void __launch_bounds__(256) k_refine_resid(DevCSR A, DevCSR M, ResidArgs r) {
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= A.n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t ab = A.rp[row], ae = A.rp[row + 1], mb = M.rp[row], me = M.rp[row + 1];
+    for (int z = 0; z < r.ninst; ++z) {
+        const c128 *X = r.Xz[z];
+        for (int c = lane; c < r.k; c += 32) {
+            c128 ax = mk<double>(0, 0);
+            for (int64_t p = ab; p < ae; ++p) fma_acc(ax, A.v[p], X[(int64_t)A.ci[p] * r.ldx + c]);
+            double mr = 0.0, mi = 0.0;
+            c128 mx = mk<double>(0, 0);
+            if (M.vr) {
+                for (int64_t p = mb; p < me; ++p) {
+                    const c128 x = X[(int64_t)M.ci[p] * r.ldx + c];
+                    mr = fma(M.vr[p], x.re, mr);
+                    mi = fma(M.vr[p], x.im, mi);
+                }
+                mx = mk<double>(mr, mi);
+            } else {
+                for (int64_t p = mb; p < me; ++p) fma_acc(mx, M.v[p], X[(int64_t)M.ci[p] * r.ldx + c]);
+            }
+            const c128 b = r.Bz[z][row * r.ldb + c];
+            r.Rz[z][row * r.ldr + c] = b - ax + r.s[z] * mx;
+        }
+    }
+}
+
+void launch_refine_resid(const DevCSR &A, const DevCSR &M, const ResidArgs &r, cudaStream_t st) {
+    if (A.n == 0 || r.k == 0 || r.ninst == 0) return;
+    k_refine_resid<<<(unsigned)((A.n + 7) / 8), 256, 0, st>>>(A, M, r);
+    g_counters.launches++;
 }
 
 // ============================================================== elementwise
@@ -341,6 +647,7 @@ void launch_lincomb(const LinArgs &a, cudaStream_t st) {
     const int64_t tot = a.n * a.k;
     if (tot == 0) return;
     k_lincomb<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a);
+    g_counters.launches++;
 }
 
 // ============================================================== column norms
@@ -372,11 +679,12 @@ void launch_colnorm2(int64_t n, int64_t k, const c128 *X, int64_t ldx, double *o
     }
     k_colnorm_part<<<NORM_CTAS, 256, 0, st>>>(n, (int)k, X, ldx, part);
     k_colnorm_sum<<<(unsigned)((k + 255) / 256), 256, 0, st>>>((int)k, NORM_CTAS, part, out);
+    g_counters.launches += 2;
 }
 
 // explicit instantiations
-template void launch_gemm<double>(const GemmArgs<double> &, int, cudaStream_t);
-template void launch_gemm<float>(const GemmArgs<float> &, int, cudaStream_t);
+template void launch_gemm<double>(const GemmArgs<double> &, int, cudaStream_t, double);
+template void launch_gemm<float>(const GemmArgs<float> &, int, cudaStream_t, double);
 template void launch_diag_lu<double>(const DiagArgs<double> &, int, cudaStream_t);
 template void launch_diag_lu<float>(const DiagArgs<float> &, int, cudaStream_t);
 template void launch_assemble<double>(const AsmArgs<double> &, int, cudaStream_t);
@@ -384,6 +692,8 @@ template void launch_assemble<float>(const AsmArgs<float> &, int, cudaStream_t);
 template void launch_extend_add<double>(const EaddArgs<double> &, int, cudaStream_t);
 template void launch_extend_add<float>(const EaddArgs<float> &, int, cudaStream_t);
 template void launch_rows<double>(const RowArgs<double> &, int, cudaStream_t);
+template void launch_eye<double>(const EyeArgs<double> &, int, cudaStream_t);
+template void launch_eye<float>(const EyeArgs<float> &, int, cudaStream_t);
 template void launch_rows<float>(const RowArgs<float> &, int, cudaStream_t);
 
 }  // namespace zolo

@@ -5,6 +5,7 @@
 namespace zolo {
 
 template <class T> struct GemmArgs {
+    int bm;                              // tile height of this launch (64, or 128 for complex64)
     const GJob *jobs[MAX_INST];
     int njobs[MAX_INST];
     int ntiles[MAX_INST];
@@ -20,6 +21,7 @@ template <class T> struct DiagArgs {
     cx<T> *inv[MAX_INST];
     int *err;
     double *minpiv;          // [ninst * njobs]
+    int *negcnt;             // optional [ninst]: pivots with negative real part
 };
 
 template <class T> struct AsmArgs {
@@ -37,7 +39,7 @@ template <class T> struct EaddArgs {
     cx<T> *pool[MAX_INST];
 };
 
-enum { ROW_GATHER = 0, ROW_SCATTER = 1, ROW_EADD = 2 };
+enum { ROW_GATHER = 0, ROW_SCATTER = 1, ROW_EADD = 2, ROW_ZERO = 3 };
 constexpr int ROWS_PER_TILE = 8;
 
 template <class T> struct RowArgs {
@@ -54,8 +56,21 @@ struct DevCSR {
     int64_t n = 0, nnz = 0;
     int64_t *rp = nullptr;
     int32_t *ci = nullptr;
-    c128 *v = nullptr;
+    c128 *v = nullptr;          // values as complex128
+    double *vr = nullptr;       // the same values when all are real (else nullptr)
 };
+
+// R_z = B_z - A X_z + s_z (M X_z) for up to MAX_INST instances (refinement residuals of
+// K = A - sigma M and K^H = A - conj(sigma) M), all blocks n x k with their own ld
+struct ResidArgs {
+    int ninst, k;
+    const c128 *Bz[MAX_INST];
+    const c128 *Xz[MAX_INST];
+    c128 *Rz[MAX_INST];
+    c128 s[MAX_INST];
+    int64_t ldb, ldx, ldr;
+};
+void launch_refine_resid(const DevCSR &A, const DevCSR &M, const ResidArgs &r, cudaStream_t st);
 
 constexpr int LIN_MAX = 8;
 struct LinArgs {
@@ -67,11 +82,29 @@ struct LinArgs {
     c128 *Y;
 };
 
-template <class T> void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st);
+// Every launch helper counts its launches; GEMM launches can also be bracketed by
+// events (profiling on) so that a caller can read their summed device time.
+struct LaunchCounters {
+    int64_t launches = 0;          // all kernels of the library
+    int64_t gemm_launches = 0;     // timed GEMM launches
+    double gemm_flops = 0.0;       // executed flops of the timed GEMM jobs (8 m n k each)
+};
+LaunchCounters &counters();
+void count_launch(int64_t n = 1);
+void prof_set(int mask);          // bit 0: complex64 GEMMs, bit 1: complex128 GEMMs
+double prof_collect_ms();          // synchronises the recorded events, returns the summed time
+template <class T> void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops = 0.0);
 template <class T> void launch_diag_lu(const DiagArgs<T> &g, int ninst, cudaStream_t st);
 template <class T> void launch_assemble(const AsmArgs<T> &g, int ninst, cudaStream_t st);
 template <class T> void launch_extend_add(const EaddArgs<T> &g, int ninst, cudaStream_t st);
 template <class T> void launch_rows(const RowArgs<T> &g, int ninst, cudaStream_t st);
+// unit diagonals: for each job, P[dst + i (rows + 1)] = 1 and P[dst + rows^2 + i (rows + 1)] = 1
+template <class T> struct EyeArgs {
+    const RJob *jobs;
+    int njobs, ntiles;
+    cx<T> *P[MAX_INST];
+};
+template <class T> void launch_eye(const EyeArgs<T> &g, int ninst, cudaStream_t st);
 void launch_spmm(const DevCSR &M, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, c128 s, bool acc,
                  cudaStream_t st);
 void launch_lincomb(const LinArgs &a, cudaStream_t st);

@@ -6,8 +6,10 @@
 //   is the small least-squares problem  min || beta_c e1 - (Hbar_m + s Ibar) z ||.
 // Arnoldi uses classical Gram-Schmidt applied twice.  The least squares are solved by
 // complex Givens rotations kept per (column, shift) and extended by one column per step;
-// the step count m is the first one at which every (column, shift) residual is below
-// gmres_tol * beta_c (the same m for the whole block).  Finally
+// the step count m is the first one at which, for every column, the error bound
+//   sum_s |omega_s| res_s / sqrt(l2^2 + |s|^2) <= gmres_tol * beta_c
+// holds (same m for the whole block; G is B-normal with real spectrum outside (-l2, l2),
+// so the bound follows from ||(G + s)^-1|| <= 1/dist(-s, spec G)).  Finally
 //   Y = X/2 + sum_j V_j zeta_j,  zeta = sum_s omega_s z_s,  omega_s = M a_j / 4.
 //
 // Algorithm 1: Y = R(B^-1 A) Q, then the projected pencil (Y^H A Y, Y^H B Y) is solved by
@@ -382,13 +384,14 @@ int gemm1(zolo_factor_s *h, cudaStream_t st, Buf &jobbuf, const c128 *A, const c
     if (rc) return rc;
     GemmArgs<double> g;
     std::memset(&g, 0, sizeof(g));
+    g.bm = 64;
     g.jobs[0] = (const GJob *)jobbuf.p;
     g.njobs[0] = 1;
     g.ntiles[0] = tiles;
     g.A[0] = A;
     g.B[0] = B;
     g.C[0] = C;
-    launch_gemm<double>(g, 1, st);
+    launch_gemm<double>(g, 1, st, 8.0 * j.m * j.n * j.k);
     return cuda_check(cudaGetLastError(), "gemm1");
 }
 
@@ -400,6 +403,7 @@ GJob job(int64_t a, int ars, int acs, int64_t b, int brs, int bcs, int64_t c, in
     j.b = b; j.brs = brs; j.bcs = bcs;
     j.c = c; j.crs = crs; j.ccs = ccs;
     j.m = m; j.n = n; j.k = k; j.flags = flags;
+    j.ks = 1;
     return j;
 }
 
@@ -425,12 +429,12 @@ static KrylovWork &work(zolo_factor_s *h) {
 }
 
 // ---------------------------------------------------------------- GMRES driver
-int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st,
-                zolo_stats *stats) {
+static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy,
+                       cudaStream_t st, zolo_stats *stats) {
     KrylovWork &w = work(h);
     const int64_t n = h->n;
     const int mmax = std::max(1, h->opts.gmres_m_max > 0 ? h->opts.gmres_m_max : 100);
-    const double tol = h->opts.gmres_tol > 0 ? h->opts.gmres_tol : 1e-12;
+    const double tol = h->gmres_tol_now > 0 ? h->gmres_tol_now : (h->opts.gmres_tol > 0 ? h->opts.gmres_tol : 1e-12);
     const int r2 = h->fi.r2, ns = 2 * r2;
     const int hld = mmax + 1;
     const int64_t blk = n * k;
@@ -459,7 +463,7 @@ int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
     if (!rc) rc = grow(h, w.H, (size_t)k * hld * hld * sizeof(c128));
     if (!rc) rc = grow(h, w.h, (size_t)(mmax + 1) * k * sizeof(c128));
     if (!rc) rc = grow(h, w.part, (size_t)RED_CTAS * JT * k * sizeof(double2));
-    if (!rc) rc = grow(h, w.nrm, (size_t)k * sizeof(double));
+    if (!rc) rc = grow(h, w.nrm, (size_t)2 * k * sizeof(double));
     if (!rc) rc = grow(h, w.beta, (size_t)k * sizeof(double));
     if (!rc) rc = grow(h, w.shifts, (size_t)ns * sizeof(c128));
     if (!rc) rc = grow(h, w.omega, (size_t)ns * sizeof(c128));
@@ -507,6 +511,7 @@ int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
         launch_lincomb(a, st);
         launch_colnorm2(n, k, w.vhost[0], k, nrm, st);
         k_normalize<<<nblk(blk), 256, 0, st>>>(n, (int)k, nrm, w.vhost[0], nullptr, hld, 0);
+        count_launch();
         // beta = sqrt(nrm): reuse the normalise kernel's formula on a k-vector
     }
     {
@@ -521,38 +526,69 @@ int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
     }
     int m = 0;
     double worst = 0.0;
-    std::vector<double> hres(pairs);
+    std::vector<double> hres(pairs), hnorm(2 * k);
     for (int i = 0; i < mmax; ++i) {
         rc = ensure_block(i + 1);
         if (rc) return rc;
         c128 *Wv = w.vhost[i + 1];
         rc = apply_inner(h, k, w.vhost[i], k, Wv, k, st);
         if (rc) return rc;
-        for (int pass = 0; pass < 2; ++pass) {          // classical Gram-Schmidt, twice
+        // classical Gram-Schmidt with selective re-orthogonalisation (Kahan-Parlett / DGKS):
+        // the second pass runs when some column lost more than 1/sqrt(2) of its norm
+        launch_colnorm2(n, k, Wv, k, nrm + k, st);
+        for (int pass = 0; pass < 2; ++pass) {
             for (int j0 = 0; j0 <= i; j0 += JT) {
                 const int nj = std::min(JT, i + 1 - j0);
                 k_multidot<<<RED_CTAS, 256, 0, st>>>(n, (int)k, Vp, j0, nj, Wv, (double2 *)w.part.p);
+                count_launch();
                 k_multidot_sum<<<nblk((int64_t)nj * k), 256, 0, st>>>((int)k, nj, RED_CTAS, (const double2 *)w.part.p,
                                                                      hv, j0, H, hld, i);
+                count_launch();
             }
             k_multiaxpy<<<nblk(blk), 256, 0, st>>>(n, (int)k, Vp, i + 1, hv, Wv);
+            count_launch();
+            if (pass == 0) {
+                launch_colnorm2(n, k, Wv, k, nrm, st);
+                rc = cuda_check(cudaMemcpyAsync(hnorm.data(), nrm, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, st),
+                                "cgs norms");
+                if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "cgs norms");
+                if (rc) return rc;
+                bool again = false;
+                for (int64_t c = 0; c < k && !again; ++c) again = hnorm[c] < 0.5 * hnorm[k + c];   // squared norms
+                if (!again) break;
+            }
         }
         launch_colnorm2(n, k, Wv, k, nrm, st);
         k_normalize<<<nblk(blk), 256, 0, st>>>(n, (int)k, nrm, Wv, H, hld, i);
+        count_launch();
         k_lsq_step<<<nblk((int64_t)pairs, 128), 128, 0, st>>>((int)k, ns, (const c128 *)w.shifts.p, H, hld, i, beta, S, mmax,
                                                          res);
+        count_launch();
         rc = cuda_check(cudaMemcpyAsync(hres.data(), res, pairs * sizeof(double), cudaMemcpyDeviceToHost, st), "res");
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "gmres step");
         if (rc) return rc;
+        // error bound of the filtered column: || sum_s omega_s (G + s)^-1 r_s || <=
+        // sum_s |omega_s| res_s / dist(-s, spec G), spec G real outside (-l2, l2), s imaginary
         worst = 0.0;
-        for (double v : hres) worst = std::max(worst, std::isfinite(v) ? v : 1e300);
+        for (int64_t c = 0; c < k; ++c) {
+            double e = 0.0;
+            for (int t = 0; t < ns; ++t) {
+                const double v = hres[c * ns + t];
+                e += std::hypot(om[t].re, om[t].im) * (std::isfinite(v) ? v : 1e300) /
+                     std::sqrt(h->fi.ell2 * h->fi.ell2 + sh[t].im * sh[t].im);
+            }
+            worst = std::max(worst, e);
+        }
         m = i + 1;
         if (worst <= tol) break;
     }
     k_lsq_solve<<<nblk((int64_t)pairs, 128), 128, 0, st>>>((int)k, ns, m, S, mmax, (const c128 *)w.omega.p,
                                                       (c128 *)w.zall.p);
+    count_launch();
     k_zeta<<<nblk((int64_t)k * m), 256, 0, st>>>((int)k, ns, m, mmax, (const c128 *)w.zall.p, (c128 *)w.zeta.p);
+    count_launch();
     k_combine<<<nblk(blk), 256, 0, st>>>(n, (int)k, X, ldx, Vp, m, (const c128 *)w.zeta.p, Y, ldy);
+    count_launch();
     rc = cuda_check(cudaGetLastError(), "gmres");
     if (rc) return rc;
     h->stats.n_gmres = m;
@@ -563,6 +599,42 @@ int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
         stats->n_solv = (int64_t)h->r1 * k * m;
     }
     if (worst > tol) return set_error(ZOLO_ENOCONV, "GMRES reached gmres_m_max without meeting gmres_tol");
+    return ZOLO_OK;
+}
+
+// The columns of X are independent GMRES problems: process them in chunks whose Krylov
+// basis, (m_max + 1) n x chunk complex128 blocks, fits a memory budget (100 GiB, or 60%
+// of the free device memory if that is smaller).
+int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st,
+                zolo_stats *stats) {
+    const int mmax = std::max(1, h->opts.gmres_m_max > 0 ? h->opts.gmres_m_max : 100);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const double budget = std::min(100.0 * (1ull << 30), 0.6 * (double)fr);
+    const double per_col = (double)(mmax + 1) * h->n * sizeof(c128);
+    int64_t chunk = std::max<int64_t>(1, (int64_t)(budget / per_col));
+    if (chunk >= 32) chunk = chunk / 32 * 32;
+    chunk = std::min(chunk, k);
+    const int64_t nch = (k + chunk - 1) / chunk;
+    chunk = (k + nch - 1) / nch;                        // balance the chunks
+    int worst_rc = ZOLO_OK, m_all = 0;
+    double res_all = 0.0;
+    for (int64_t c0 = 0; c0 < k; c0 += chunk) {
+        const int64_t kc = std::min(chunk, k - c0);
+        int rc = gmres_block(h, kc, X + c0, ldx, Y + c0, ldy, st, stats);
+        if (rc && rc != ZOLO_ENOCONV) return rc;
+        if (rc) worst_rc = rc;
+        m_all = std::max(m_all, h->stats.n_gmres);
+        res_all = std::max(res_all, h->stats.gmres_res);
+    }
+    h->stats.n_gmres = m_all;
+    h->stats.gmres_res = res_all;
+    if (stats) {
+        stats->n_gmres = m_all;
+        stats->gmres_res = res_all;
+        stats->n_solv = (int64_t)h->r1 * k * m_all;
+    }
+    if (worst_rc) return set_error(worst_rc, "GMRES reached gmres_m_max without meeting gmres_tol");
     return ZOLO_OK;
 }
 
@@ -577,10 +649,13 @@ static int jacobi_eig(zolo_factor_s *h, KrylovWork &w, int k, c128 *A, c128 *V, 
     if (!rc) rc = grow(h, w.dvec, (size_t)k * sizeof(double));
     if (rc) return rc;
     k_hermitize<<<nblk((int64_t)k * k), 256, 0, st>>>(k, A);
+    count_launch();
     k_eye<<<nblk((int64_t)k * k), 256, 0, st>>>(k, V);
+    count_launch();
     double off[2] = {0, 0};
     for (int sweep = 0; sweep < 30; ++sweep) {
         k_offnorm<<<1, 256, 0, st>>>(k, A, (double *)w.off.p);
+        count_launch();
         rc = cuda_check(cudaMemcpyAsync(off, w.off.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "off");
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "jacobi");
         if (rc) return rc;
@@ -589,12 +664,15 @@ static int jacobi_eig(zolo_factor_s *h, KrylovWork &w, int k, c128 *A, c128 *V, 
         if (off[0] <= 1e-30 * std::max(off[1], 1e-300) || k == 1) break;
         for (int r = 0; r < kk - 1; ++r) {
             k_jacobi_cols<<<kk / 2, 128, 0, st>>>(k, kk, r, A, V, (Rot *)w.rot.p);
+            count_launch();
             k_jacobi_rows<<<kk / 2, 128, 0, st>>>(k, kk, r, A, (const Rot *)w.rot.p);
+            count_launch();
         }
     }
     if (off[0] > 1e-24 * std::max(off[1], 1e-300) && k > 1)
         return set_error(ZOLO_ENOCONV, "Jacobi eigensolver did not converge");
     k_diag<<<nblk(k), 256, 0, st>>>(k, A, (double *)w.dvec.p);
+    count_launch();
     d.assign(k, 0.0);
     rc = cuda_check(cudaMemcpyAsync(d.data(), w.dvec.p, k * sizeof(double), cudaMemcpyDeviceToHost, st), "eig");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "eig");
@@ -613,6 +691,7 @@ static int gather_cols(zolo_factor_s *h, KrylovWork &w, int k, const c128 *V, co
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "gather");
     if (rc) return rc;
     k_gather_cols<<<nblk((int64_t)k * kt), 256, 0, st>>>(k, kt, V, (const int *)w.idx.p, (const double *)w.scl.p, W);
+    count_launch();
     return cuda_check(cudaGetLastError(), "gather");
 }
 
@@ -641,14 +720,16 @@ static int gram(zolo_factor_s *h, KrylovWork &w, int64_t n, int k, const c128 *Y
     if (rc) return rc;
     GemmArgs<double> g;
     std::memset(&g, 0, sizeof(g));
+    g.bm = 64;
     g.jobs[0] = (const GJob *)w.jobs.p;
     g.njobs[0] = parts;
     g.ntiles[0] = tiles;
     g.A[0] = Y;
     g.B[0] = Z;
     g.C[0] = (c128 *)w.gram_part.p;
-    launch_gemm<double>(g, 1, st);
+    launch_gemm<double>(g, 1, st, 8.0 * k * k * (double)n);
     k_sum_parts<<<nblk((int64_t)k * k), 256, 0, st>>>((int64_t)k * k, parts, (const c128 *)w.gram_part.p, C);
+    count_launch();
     return cuda_check(cudaGetLastError(), "gram");
 }
 
@@ -682,6 +763,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         rc = cuda_check(cudaMemcpyAsync(Q, X0, blk * sizeof(c128), cudaMemcpyDeviceToDevice, st), "X0");
     } else {
         k_randn<<<nblk(blk), 256, 0, st>>>(blk, h->opts.seed, Q);
+        count_launch();
         rc = cuda_check(cudaGetLastError(), "randn");
     }
     if (rc) return rc;
@@ -699,9 +781,20 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
     cudaEventCreate(&e2);
     float t_apply = 0.f, t_rr = 0.f;
     int n_gm = 0;
+    bool gmres_short = false;
     for (it = 1; it <= itmax; ++it) {
         cudaEventRecord(e0, st);
+        // The first application starts from a random block: its filtered output is re-filtered
+        // by the next iteration, so a loose GMRES tolerance (1e-6) is enough there; later
+        // applications start from Ritz vectors and use gmres_tol.
+        const double gt = h->opts.gmres_tol > 0 ? h->opts.gmres_tol : 1e-12;
+        h->gmres_tol_now = (it == 1 && itmax > 1) ? std::max(gt, 1e-6) : gt;
         rc = gmres_apply(h, kq, Q, kq, Y, kq, st, nullptr);          // Y = R(B^-1 A) Q
+        h->gmres_tol_now = 0.0;
+        if (rc == ZOLO_ENOCONV) {                                    // use the block anyway
+            gmres_short = true;
+            rc = ZOLO_OK;
+        }
         if (rc) break;
         n_gm += h->stats.n_gmres;
         cudaEventRecord(e1, st);
@@ -715,10 +808,15 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         if (rc) break;
         double mumax = 0.0;
         for (double x : mu) mumax = std::max(mumax, x);
+        // directions whose B-norm is at the level of the filtered block's own error are
+        // noise: drop below max(drop_tol, (10 * GMRES tolerance of this pass)^2) * max mu
+        const double tol_it = (it == 1 && itmax > 1) ? std::max(h->opts.gmres_tol > 0 ? h->opts.gmres_tol : 1e-12, 1e-6)
+                                                     : (h->opts.gmres_tol > 0 ? h->opts.gmres_tol : 1e-12);
+        const double drop_it = std::max(drop, 100.0 * tol_it * tol_it);
         std::vector<int> keep;
         std::vector<double> scl;
         for (int i = 0; i < kq; ++i)
-            if (mu[i] > drop * mumax) {
+            if (mu[i] > drop_it * mumax) {
                 keep.push_back(i);
                 scl.push_back(1.0 / std::sqrt(mu[i]));
             }
@@ -751,6 +849,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         rc = cuda_check(cudaMemcpyAsync(w.dvec.p, lam.data(), kq * sizeof(double), cudaMemcpyHostToDevice, st), "lam");
         if (rc) break;
         k_resid_block<<<nblk(n * kq), 256, 0, st>>>(n, kq, AY, BY, (const double *)w.dvec.p, R);
+        count_launch();
         rc = grow(h, w.nrm, (size_t)3 * kq * sizeof(double));
         if (rc) break;
         double *nr = (double *)w.nrm.p;
@@ -814,13 +913,16 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "sel");
         if (rc) return rc;
         k_select_cols<<<nblk(n * nf), 256, 0, st>>>(n, nf, Q, kq, (const int *)w.idx.p, evecs, ldv);
+        count_launch();
         rc = cuda_check(cudaGetLastError(), "evecs");
         if (rc) return rc;
     }
     rc = cuda_check(cudaStreamSynchronize(st), "eigs");
     if (rc) return rc;
     if (stats) *stats = h->stats;
-    if (!converged) return set_error(ZOLO_ENOCONV, "eigenpair residuals above tol after n_iter_max iterations");
+    if (!converged)
+        return set_error(ZOLO_ENOCONV, gmres_short ? "eigenpair residuals above tol (GMRES also hit gmres_m_max)"
+                                                   : "eigenpair residuals above tol after n_iter_max iterations");
     return ZOLO_OK;
 }
 

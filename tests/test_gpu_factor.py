@@ -83,4 +83,6 @@ def test_refactor_is_repeatable():
     X1 = host(fac.solve(1, dev(Bk), herm=True))
     fac.refactor()
     X2 = host(fac.solve(1, dev(Bk), herm=True))
-    assert np.array_equal(X1, X2)
+    # the factorisation is deterministic; the solves split long inner products over
+    # CTAs with atomic adds, so results agree to rounding
+    assert colrel(X2, X1) < 1e-13
