@@ -175,6 +175,17 @@ def checked_gaps(Z, pen, sym, opts):
     return GAPS
 
 
+def combine_ranks(dist, ms, conv, device):
+    """Whole-job figures of N replicas: the slowest rank's time and the summed count of
+    converged eigenpairs (no collective on the data path; only these two scalars)."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(conv)], device=device, dtype=torch.float64)
+    dist.all_reduce(c)
+    return float(t.item()), int(c.item())
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -236,12 +247,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        c = torch.tensor([conv], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c)
-        conv = int(c.item())
+        ms, conv = combine_ranks(dist, ms, conv, "cuda")
     value = conv / (ms * args.steps / 1e3)
 
     # ---- end to end: the one-call driver from host CSR, results copied back to the host

@@ -111,7 +111,8 @@ typedef struct {
                               <= gmres_tol * ||x_c|| (res_s: shift s least-squares
                               residual; default 1e-12)                           */
     int32_t  refine_max;   /* refinement steps per shifted solve, MIXED (default 8) */
-    double   refine_tol;   /* refinement stops at ||b - K x|| <= refine_tol ||b|| (1e-13) */
+    double   refine_tol;   /* refinement stops at ||b - K x|| <= refine_tol ||b|| (1e-12),
+                              or when the residual stalls below 1e-10 (FP64 floor)  */
     int32_t  n_iter_max;   /* subspace iterations at most (default 4)             */
     double   tol;          /* eigenpair residual ||Ax - lam Bx||/(||A||_inf ||x||) (1e-10) */
     double   drop_tol;     /* B-Gram eigenvalues below max(drop_tol, (10 tol_g)^2) * max

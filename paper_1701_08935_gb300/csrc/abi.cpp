@@ -25,7 +25,7 @@ void zolo_opts_default(zolo_opts *o) {
     o->gmres_m_max = 100;
     o->gmres_tol = 1e-12;
     o->refine_max = 8;
-    o->refine_tol = 1e-13;
+    o->refine_tol = 1e-12;
     o->n_iter_max = 4;
     o->tol = 1e-10;
     o->drop_tol = 1e-14;

@@ -101,6 +101,7 @@ struct zolo_factor_s {
 
     zolo::KrylovWork *kw = nullptr;
     double gmres_tol_now = 0.0;                    // tolerance of the current filter application
+    bool inner_failed = false;                     // an inner solve of the current GMRES failed
     int *d_negcnt = nullptr;                       // inertia: negative pivots per pole
     bool count_neg = false;
     zolo_stats stats;

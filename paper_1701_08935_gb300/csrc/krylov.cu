@@ -18,6 +18,7 @@
 // a parallel cyclic Jacobi method (round-robin pairing, two launches per round).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 #include "factor.h"
@@ -520,6 +521,10 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "beta");
         if (rc) return rc;
         for (auto &x : hn) x = std::sqrt(x);
+        if (h->opts.verbose)
+            std::fprintf(stderr, "[zolo] gmres block k=%lld ldx=%lld: ||x_c|| in [%.3e, %.3e]\n", (long long)k,
+                         (long long)ldx, *std::min_element(hn.begin(), hn.end()),
+                         *std::max_element(hn.begin(), hn.end()));
         rc = cuda_check(cudaMemcpyAsync(beta, hn.data(), k * sizeof(double), cudaMemcpyHostToDevice, st), "beta");
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "beta");
         if (rc) return rc;
@@ -532,7 +537,10 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
         if (rc) return rc;
         c128 *Wv = w.vhost[i + 1];
         rc = apply_inner(h, k, w.vhost[i], k, Wv, k, st);
-        if (rc) return rc;
+        if (rc) {                                          // a failed inner solve is not a short GMRES
+            h->inner_failed = true;
+            return rc;
+        }
         // classical Gram-Schmidt with selective re-orthogonalisation (Kahan-Parlett / DGKS):
         // the second pass runs when some column lost more than 1/sqrt(2) of its norm
         launch_colnorm2(n, k, Wv, k, nrm + k, st);
@@ -580,6 +588,8 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
             worst = std::max(worst, e);
         }
         m = i + 1;
+        if (h->opts.verbose && (i < 3 || worst <= tol))
+            std::fprintf(stderr, "[zolo]   step %d: error bound %.3e (tol %.1e)\n", i + 1, worst, tol);
         if (worst <= tol) break;
     }
     k_lsq_solve<<<nblk((int64_t)pairs, 128), 128, 0, st>>>((int)k, ns, m, S, mmax, (const c128 *)w.omega.p,
@@ -619,10 +629,11 @@ int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
     chunk = (k + nch - 1) / nch;                        // balance the chunks
     int worst_rc = ZOLO_OK, m_all = 0;
     double res_all = 0.0;
+    h->inner_failed = false;
     for (int64_t c0 = 0; c0 < k; c0 += chunk) {
         const int64_t kc = std::min(chunk, k - c0);
         int rc = gmres_block(h, kc, X + c0, ldx, Y + c0, ldy, st, stats);
-        if (rc && rc != ZOLO_ENOCONV) return rc;
+        if (rc && (rc != ZOLO_ENOCONV || h->inner_failed)) return rc;
         if (rc) worst_rc = rc;
         m_all = std::max(m_all, h->stats.n_gmres);
         res_all = std::max(res_all, h->stats.gmres_res);
@@ -791,7 +802,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         h->gmres_tol_now = (it == 1 && itmax > 1) ? std::max(gt, 1e-6) : gt;
         rc = gmres_apply(h, kq, Q, kq, Y, kq, st, nullptr);          // Y = R(B^-1 A) Q
         h->gmres_tol_now = 0.0;
-        if (rc == ZOLO_ENOCONV) {                                    // use the block anyway
+        if (rc == ZOLO_ENOCONV && !h->inner_failed) {               // GMRES step cap: use the block
             gmres_short = true;
             rc = ZOLO_OK;
         }
@@ -821,6 +832,9 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
                 scl.push_back(1.0 / std::sqrt(mu[i]));
             }
         const int kt = (int)keep.size();
+        if (h->opts.verbose)
+            std::fprintf(stderr, "[zolo] iteration %d: GMRES steps %d, B-Gram mu in [%.3e, %.3e], kept %d of %d\n", it,
+                         h->stats.n_gmres, *std::min_element(mu.begin(), mu.end()), mumax, kt, kq);
         if (kt == 0) {
             rc = set_error(ZOLO_ENOCONV, "filtered block vanished (no eigenvalues in the interval?)");
             break;
@@ -885,6 +899,10 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         }
         h->stats.max_resid = worst;
         h->stats.relerr = relerr;
+        if (h->opts.verbose)
+            std::fprintf(stderr, "[zolo] iteration %d: Ritz values in [%.6f, %.6f], %d inside (a, b), worst residual %.3e\n",
+                         it, *std::min_element(lam.begin(), lam.end()), *std::max_element(lam.begin(), lam.end()),
+                         (int)sel.size(), worst);
         if (worst <= tol) {
             converged = true;
             break;
