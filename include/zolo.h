@@ -214,6 +214,20 @@ int  zolo_factor_get_stats(zolo_factor_h h, zolo_stats *out);
  * overlap.  0 <= pole < r1.                                                      */
 int  zolo_solve(zolo_factor_h h, int32_t pole, int32_t herm, int64_t k, const void *Bk,
                 int64_t ldb, void *X, int64_t ldx, void *stream);
+/* zolo_solve without device allocation (the paper has no counterpart: this serves callers
+ * that must not allocate on the calls they repeat -- work recorded into a CUDA graph by
+ * stream capture, where cudaMalloc is not allowed, allocation-free real-time loops, or hosts
+ * whose device memory pool belongs to someone else).  Same result as zolo_solve for a
+ * complex128 (ZOLO_PREC_FP64) handle; the front workspaces come from one fixed device array
+ * of 32 MiB that every GPU loading the library holds until exit, so
+ * (rows of all fronts + n) * k * 16 bytes must fit in it (EINVAL otherwise, with the sizes).
+ * Set-up: create the handle and call zolo_solve once with the same k (both allocate); the
+ * first zolo_solve_noalloc call on a device looks up the array's device address, so make
+ * that first call before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (each call clears what it needs): calls that overlap on the GPU
+ * race.  EINVAL for MIXED handles or a k without a schedule.  Synchronises `stream`.     */
+int  zolo_solve_noalloc(zolo_factor_h h, int32_t pole, int32_t herm, int64_t k, const void *Bk,
+                        int64_t ldb, void *X, int64_t ldx, void *stream);
 /* Y := A X (which = 0) or B X (which = 1), device blocks (SpMM with the uploaded CSR). */
 int  zolo_matmul(zolo_factor_h h, int32_t which, int64_t k, const void *X, int64_t ldx,
                  void *Y, int64_t ldy, void *stream);

@@ -106,6 +106,7 @@ _sig("zolo_profile_end", C.c_int, [_vp, _P(_i64), _P(_i64), _P(_dbl), _P(_dbl)])
 _sig("zolo_factor_destroy", None, [_vp])
 _sig("zolo_factor_get_stats", C.c_int, [_vp, _P(Stats)])
 _sig("zolo_solve", C.c_int, [_vp, _i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp])
+_sig("zolo_solve_noalloc", C.c_int, [_vp, _i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp])
 _sig("zolo_matmul", C.c_int, [_vp, _i32, _i64, _vp, _i64, _vp, _i64, _vp])
 _sig("zolo_apply_inner", C.c_int, [_vp, _i64, _vp, _i64, _vp, _i64, _vp])
 _sig("zolo_apply", C.c_int, [_vp, _i64, _vp, _i64, _vp, _i64, _P(Stats), _vp])
@@ -117,7 +118,7 @@ _sig("zolo_eigs", C.c_int, [_P(Csr), _P(Csr), _dbl, _dbl, _i64, _P(FilterSpec), 
 EXPORTED = ["zolo_opts_default", "zolo_strerror", "zolo_last_error", "zolo_version", "zolo_filter_build",
             "zolo_filter_get_info", "zolo_filter_eval", "zolo_filter_destroy", "zolo_analyze",
             "zolo_symbolic_get_info", "zolo_symbolic_export", "zolo_symbolic_destroy", "zolo_factor",
-            "zolo_refactor", "zolo_inertia", "zolo_profile_begin", "zolo_profile_end", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
+            "zolo_refactor", "zolo_inertia", "zolo_solve_noalloc", "zolo_profile_begin", "zolo_profile_end", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
             "zolo_apply_inner", "zolo_apply", "zolo_eigs_factored", "zolo_eigs"]
 
 
@@ -286,6 +287,14 @@ class Factor:
         out = out if out is not None else torch.empty_like(B)
         px, _, ldx = _blk(out, "out")
         _check(lib.zolo_solve(self.h, pole, 1 if herm else 0, k, pb, ldb, px, ldx, _stream(stream)), "zolo_solve")
+        return out
+
+    def solve_noalloc(self, pole, B, out, herm=False, stream=None):
+        """zolo_solve through the fixed no-allocation workspace (see include/zolo.h)."""
+        pb, k, ldb = _blk(B, "B")
+        px, _, ldx = _blk(out, "out")
+        _check(lib.zolo_solve_noalloc(self.h, pole, 1 if herm else 0, k, pb, ldb, px, ldx, _stream(stream)),
+               "zolo_solve_noalloc")
         return out
 
     def matmul(self, which, X, out=None, stream=None):
