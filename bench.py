@@ -89,10 +89,11 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- workload
-def make_workload():
+def make_workload(case="full"):
     from paper_1701_08935_gb300 import synth
-    pen = synth.pencil_3d_peierls(N_SIDE, seed=SEED)
-    return pen
+    if case == "small":
+        return synth.pencil_3d_peierls(32, seed=SEED, wells=4)
+    return synth.pencil_3d_peierls(N_SIDE, seed=SEED)
 
 
 # Eigengaps of the seeded 64^3 pencil around eigenvalue numbers 1000 and 1200, found by
@@ -198,13 +199,15 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     prec = Z.PREC_MIXED if args.precision == "mixed" else Z.PREC_FP64
-    pen = make_workload()
-    opts = Z.default_opts(grid=pen.dims, leaf_max=32, precision=prec, n_iter_max=1 if args.case == "profile" else 4,
+    pen = make_workload(args.case)
+    opts = Z.default_opts(grid=pen.dims, leaf_max=32, precision=prec, n_iter_max=1 if args.case != "full" else 4,
                           tol=TOL, gmres_tol=GMRES_TOL, gmres_m_max=GMRES_M_MAX)
     sym = Z.Symbolic(pen.A, pen.B, opts)
     iopts = Z.default_opts(grid=pen.dims, leaf_max=32, precision=Z.PREC_FP64)
     if args.case == "profile":
         am, ap, count_a, bm, bp, count_b = GAPS
+    elif args.case == "small":                 # profiling only: nominal buffers, no gap search
+        am, ap, count_a, bm, bp, count_b = 0.329, 0.330, 0, 0.421, 0.422, 0
     else:
         am, ap, count_a, bm, bp, count_b = checked_gaps(Z, pen, sym, iopts)
     if args.locate:
@@ -417,16 +420,18 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--locate", action="store_true", help="locate the eigengaps by inertia counts and exit")
-    ap.add_argument("--case", default="full", choices=["full", "profile"],
+    ap.add_argument("--case", default="full", choices=["full", "profile", "small"],
                     help="profile: the same workload truncated for an ncu launch list (k=150, 8 GMRES "
-                         "steps, one subspace iteration, no warm-up, no end-to-end or CPU legs)")
+                         "steps, one subspace iteration, no warm-up, no end-to-end or CPU legs); "
+                         "small: the same recipe on a 32^3 grid, truncated the same way, for ncu "
+                         "captures that must hold only a few GB on the device")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     global GAPS, K_SUB, GMRES_M_MAX
     if args.locate:
         GAPS = None
-    if args.case == "profile":
+    if args.case in ("profile", "small"):
         K_SUB, GMRES_M_MAX = 150, 8
         args.warmup, args.steps, args.no_cpu = 0, 1, True
     if args.impl == "reference":
