@@ -57,6 +57,12 @@ extern "C" {
                              pencil; Krylov basis, least squares, Gram and Rayleigh-Ritz
                              stay FP64 */
 
+/* ---- complex64 GEMM engine of the mixed-precision fronts and solves ------ */
+#define ZOLO_TC_AUTO   0  /* tcgen05 tensor cores (3xTF32 split, FP32 accumulation) for
+                             launches whose fronts average >= 256 rows, FP32 FMA for the rest */
+#define ZOLO_TC_OFF    1  /* FP32 FMA only */
+#define ZOLO_TC_ALWAYS 2  /* tensor cores for every complex64 GEMM launch */
+
 #define ZOLO_MAX_R 16     /* largest r1, r2 accepted */
 
 typedef struct {
@@ -70,7 +76,7 @@ typedef struct {
 } zolo_csr;
 
 /* Filter specification: the eigengaps (a-, a+) around a and (b-, b+) around b
- * (Section 1, "Contribution"; Algorithm 2 line 1).  a_minus may be -INFINITY (the
+ * (Section 1.2; the gap-estimation step of Algorithm 2).  a_minus may be -INFINITY (the
  * lowest slice, as in Section 3.1).  r1 / r2 are the inner (factored) and outer
  * (GMRES) Zolotarev orders; if either is <= 0 the smallest r = r1 = r2 with
  * delta0 <= eps is chosen (Remark after Algorithm 2).                       */
@@ -80,7 +86,7 @@ typedef struct {
     double  eps;
 } zolo_filter_spec;
 
-/* Everything Algorithm 2 lines 2-4 compute. */
+/* Everything the filter-construction steps of Algorithm 2 compute. */
 typedef struct {
     double  alpha, beta, gamma;         /* T(x) = gamma (x - alpha)/(x - beta)  (eq. mo) */
     double  ell1, ell2;                 /* eq. req and l2 = Zhat(l1; l1)              */
@@ -123,7 +129,7 @@ typedef struct {
                               g = gap_rel (b - a) (default 1e-2)                  */
     uint64_t seed;         /* starting block: SplitMix64-seeded normal entries     */
     int32_t  verbose;      /* 0 silent, 1 stages to stderr                         */
-    int32_t  reserved;
+    int32_t  tensor_core;  /* ZOLO_PREC_MIXED GEMMs: ZOLO_TC_AUTO (default), _OFF, _ALWAYS */
 } zolo_opts;
 
 /* Counters and timings filled by zolo_apply / zolo_eigs (n_solv as Section 3 counts it). */
@@ -163,7 +169,7 @@ const char *zolo_strerror(int status);
 const char *zolo_last_error(void);              /* thread-local detail message */
 int         zolo_version(void);                 /* 100 * major + minor */
 
-/* ---- filter (host only; Algorithm 2 lines 1-4) -------------------------- */
+/* ---- filter (host only; filter steps of Algorithm 2) ---------------------- */
 /* Build R_ab: Moebius map from eq. req, Zolotarev coefficients (Thm 1), rescaling
  * (eq. rZ), l2, partial fractions (Prop. 1, Cor. 1) and inner poles/weights (Prop. 2).
  * EINVAL unless a- < a+ < b- < b+ (a- may be -inf), 1 <= r <= ZOLO_MAX_R.       */
@@ -189,7 +195,7 @@ void zolo_symbolic_destroy(zolo_symbolic s);
 
 /* ---- numeric factorisation (device) ------------------------------------- */
 /* Upload the pencil and factor K_j = A - sigma_hat_j B, j = 1..r1, by the multifrontal
- * method on the device (Algorithm 2 line 5): no-pivot LU of every front, level by
+ * method on the device (the factorisation step of Algorithm 2): no-pivot LU of every front, level by
  * level, with the poles batched in each launch.  `sym` may be NULL (analysed here).
  * ESINGULAR on a zero / non-finite pivot.  Synchronises `stream`.               */
 int  zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbolic sym,
@@ -234,7 +240,7 @@ int  zolo_matmul(zolo_factor_h h, int32_t which, int64_t k, const void *X, int64
 /* Y := G X, the inner operator of eq. solve (r1 factored poles, conjugates via K^-H). */
 int  zolo_apply_inner(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y,
                       int64_t ldy, void *stream);
-/* Y := R_ab(B^-1 A) X by Algorithm 2 lines 9-10 (shift-invariant GMRES, one basis per
+/* Y := R_ab(B^-1 A) X by the GMRES steps of Algorithm 2 (shift-invariant GMRES, one basis per
  * column shared by the 2 r2 shifts).  X, Y: n x k device blocks, may not overlap.  */
 int  zolo_apply(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y, int64_t ldy,
                 zolo_stats *stats, void *stream);
@@ -269,6 +275,10 @@ int  zolo_profile_begin(int32_t gemm_events);
  * device time (ms) and the flops those GEMM jobs executed (8 m n k each).           */
 int  zolo_profile_end(void *stream, int64_t *launches, int64_t *gemm_launches, double *gemm_ms,
                       double *gemm_flops);
+/* The tcgen05 tensor-core share of the timed complex64 GEMM launches between the last
+ * zolo_profile_begin and zolo_profile_end: launches, summed device time (ms), executed
+ * flops (8 m n k per job).  Host values only; never fails.                         */
+int  zolo_profile_tc(int64_t *launches, double *ms, double *flops);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,7 @@ lib = C.CDLL(_LIBPATH)
 OK, EINVAL, ENOTHERM, ENOMEM, ESINGULAR, ENOCONV, ETIMEOUT, ECUDA, EGAP = range(9)
 R64, C128 = 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
+TC_AUTO, TC_OFF, TC_ALWAYS = 0, 1, 2
 MAX_R = 16
 
 _i32, _i64, _u64, _dbl, _vp = C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_void_p
@@ -56,7 +57,7 @@ class Opts(C.Structure):
     _fields_ = [("grid", _i32 * 3), ("leaf_max", _i32), ("precision", _i32), ("gmres_m_max", _i32),
                 ("gmres_tol", _dbl), ("refine_max", _i32), ("refine_tol", _dbl), ("n_iter_max", _i32),
                 ("tol", _dbl), ("drop_tol", _dbl), ("k", _i32), ("r1", _i32), ("r2", _i32),
-                ("gap_rel", _dbl), ("seed", _u64), ("verbose", _i32), ("reserved", _i32)]
+                ("gap_rel", _dbl), ("seed", _u64), ("verbose", _i32), ("tensor_core", _i32)]
 
 
 class Stats(C.Structure):
@@ -103,6 +104,7 @@ _sig("zolo_refactor", C.c_int, [_vp, _vp])
 _sig("zolo_inertia", C.c_int, [_P(Csr), _P(Csr), _vp, _P(Opts), _i32, _vp, _vp, _vp])
 _sig("zolo_profile_begin", C.c_int, [_i32])
 _sig("zolo_profile_end", C.c_int, [_vp, _P(_i64), _P(_i64), _P(_dbl), _P(_dbl)])
+_sig("zolo_profile_tc", C.c_int, [_P(_i64), _P(_dbl), _P(_dbl)])
 _sig("zolo_factor_destroy", None, [_vp])
 _sig("zolo_factor_get_stats", C.c_int, [_vp, _P(Stats)])
 _sig("zolo_solve", C.c_int, [_vp, _i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp])
@@ -118,7 +120,8 @@ _sig("zolo_eigs", C.c_int, [_P(Csr), _P(Csr), _dbl, _dbl, _i64, _P(FilterSpec), 
 EXPORTED = ["zolo_opts_default", "zolo_strerror", "zolo_last_error", "zolo_version", "zolo_filter_build",
             "zolo_filter_get_info", "zolo_filter_eval", "zolo_filter_destroy", "zolo_analyze",
             "zolo_symbolic_get_info", "zolo_symbolic_export", "zolo_symbolic_destroy", "zolo_factor",
-            "zolo_refactor", "zolo_inertia", "zolo_solve_noalloc", "zolo_profile_begin", "zolo_profile_end", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
+            "zolo_refactor", "zolo_inertia", "zolo_solve_noalloc", "zolo_profile_begin", "zolo_profile_end",
+            "zolo_profile_tc", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
             "zolo_apply_inner", "zolo_apply", "zolo_eigs_factored", "zolo_eigs"]
 
 
@@ -157,7 +160,7 @@ class HostCsr:
 
 
 class Filter:
-    """R_ab of eq. R2 with every constant of Algorithm 2 lines 2-4 (host-built)."""
+    """R_ab of eq. R2 with every constant of Algorithm 2's filter-construction steps (host-built)."""
 
     def __init__(self, a_minus, a_plus, b_minus, b_plus, r1=2, r2=2, eps=0.0):
         spec = FilterSpec(a_minus, a_plus, b_minus, b_plus, r1, r2, eps)
@@ -242,7 +245,10 @@ def profile_end(stream=None):
     n, ng, ms, fl = _i64(0), _i64(0), _dbl(0), _dbl(0)
     _check(lib.zolo_profile_end(_stream(stream), C.byref(n), C.byref(ng), C.byref(ms), C.byref(fl)),
            "zolo_profile_end")
-    return {"launches": n.value, "gemm_launches": ng.value, "gemm_ms": ms.value, "gemm_flops": fl.value}
+    tn, tms, tfl = _i64(0), _dbl(0), _dbl(0)
+    _check(lib.zolo_profile_tc(C.byref(tn), C.byref(tms), C.byref(tfl)), "zolo_profile_tc")
+    return {"launches": n.value, "gemm_launches": ng.value, "gemm_ms": ms.value, "gemm_flops": fl.value,
+            "tc_launches": tn.value, "tc_ms": tms.value, "tc_flops": tfl.value}
 
 
 def _stream(stream):

@@ -1,4 +1,4 @@
-// Multifrontal factorisation of K_j = A - sigma_hat_j B (Algorithm 2 line 5) and the
+// Multifrontal factorisation of K_j = A - sigma_hat_j B (the factorisation step of Algorithm 2) and the
 // block triangular solves with K_j and K_j^H that eq. solve needs, on the device.
 //
 // Fronts are dense column-major (pivots, update rows)^2 blocks, stored level by level in
@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include "factor.h"
+#include "df64.cuh"
 
 namespace zolo {
 
@@ -82,38 +83,104 @@ GJob make_job(int64_t a, int ars, int acs, int64_t b, int brs, int bcs, int64_t 
     return j;
 }
 
-// Precision of the launches being planned (complex64 launches may use 128-row tiles).
+// Precision of the launches being planned (complex64 launches may use 128-row tiles)
+// and the tensor-core policy (zolo_opts.tensor_core) for complex64 launches.
 thread_local bool g_plan_c64 = false;
+thread_local int g_plan_tc = ZOLO_TC_AUTO;
+// Tile -> job map of the launches being planned (appended by add_gemm when set).
+thread_local std::vector<int32_t> *g_plan_tmap = nullptr;
+// Complex64 launches whose jobs average at least this many rows go to the tensor cores.
+constexpr double TC_MIN_ROWS = 128.0;
 
 // Append a launch of GEMM jobs (empty products dropped) and return its descriptor.
-// Tile height: 128 rows for complex64 launches whose jobs average >= 256 rows, else 64.
-// With allow_split, a launch with fewer than ~4 waves of tiles splits the kk extent of its
-// accumulating jobs (GJ_SUB / GJ_ACC, kk >= 512) over several CTAs (atomic adds).
-Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs, bool allow_split = false) {
+// Complex64 launches whose jobs average >= TC_MIN_ROWS rows run on the tensor-core kernel
+// (128 x <= 256 tiles; every complex64 launch with ZOLO_TC_ALWAYS, none with ZOLO_TC_OFF,
+// where they take 128 x 64 FP32 tiles instead); other launches take 64 x 64 tiles.
+// With allow_split, a launch with fewer than ~4 waves of tiles (2 for the tensor-core
+// kernel, one CTA per SM) splits the kk extent of its accumulating jobs (GJ_SUB / GJ_ACC,
+// kk >= 512) over several CTAs (atomic adds).
+Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool allow_split = false) {
     Launch L;
     L.off = (int64_t)all.size();
-    double msum = 0.0;
+    double msum = 0.0, nsum = 0.0;
     int cnt = 0;
-    for (const GJob &j : jobs)
+    for (const GJob &j : jobs_in)
         if (j.m > 0 && j.n > 0 && j.k > 0) {
             msum += j.m;
+            nsum += j.n;
             ++cnt;
         }
-    L.bm = (g_plan_c64 && cnt && msum / cnt >= 256.0) ? 128 : 64;
+    // Short, wide products (a front's few pivot rows times a block of columns) fill the
+    // 128-row tensor-core tiles only when taken transposed: C^T = op(B)^T op(A)^T, a swap
+    // of operands, strides and conjugation flags.  Only solve launches (allow_split), whose
+    // C never aliases A or B, are transposed; the caller swaps the A and B base pointers.
+    std::vector<GJob> tj;
+    const std::vector<GJob> *src = &jobs_in;
+    if (g_plan_c64 && allow_split && cnt && g_plan_tc != ZOLO_TC_OFF && msum / cnt < TC_MIN_ROWS &&
+        nsum / cnt >= TC_MIN_ROWS) {
+        tj = jobs_in;
+        for (GJob &j : tj) {
+            std::swap(j.a, j.b);
+            const int ars = j.bcs, acs = j.brs, brs = j.acs, bcs = j.ars;
+            j.ars = ars; j.acs = acs; j.brs = brs; j.bcs = bcs;
+            std::swap(j.crs, j.ccs);
+            std::swap(j.m, j.n);
+            const int f = j.flags & ~(GJ_CONJA | GJ_CONJB);
+            j.flags = f | ((j.flags & GJ_CONJA) ? GJ_CONJB : 0) | ((j.flags & GJ_CONJB) ? GJ_CONJA : 0);
+        }
+        src = &tj;
+        L.swap_ab = true;
+        std::swap(msum, nsum);
+    }
+    const std::vector<GJob> &jobs = *src;
+    const bool big = cnt && msum / cnt >= 256.0;
+    L.bm = (g_plan_c64 && big) ? 128 : 64;
+    if (g_plan_c64 && cnt &&
+        (g_plan_tc == ZOLO_TC_ALWAYS || (g_plan_tc == ZOLO_TC_AUTO && msum / cnt >= TC_MIN_ROWS))) {
+        L.bm = 128;
+        L.bn = 256;
+    }
+    auto splittable = [](const GJob &j) { return (j.flags & (GJ_SUB | GJ_ACC)) && j.k >= 512; };
+    auto split_of = [&](const GJob &j, int f) { return splittable(j) ? std::max(1, std::min({f, j.k / 256, 16})) : 1; };
+    auto tiles_of = [&](const GJob &j) { return ((j.m + L.bm - 1) / L.bm) * ((j.n + L.bn - 1) / L.bn); };
     int base = 0;
     for (const GJob &j : jobs)
-        if (j.m > 0 && j.n > 0 && j.k > 0) base += ((j.m + L.bm - 1) / L.bm) * ((j.n + 63) / 64);
-    const int target = 4 * 152;
-    const int factor = (allow_split && base > 0 && base < target) ? (target + base - 1) / base : 1;
+        if (j.m > 0 && j.n > 0 && j.k > 0) base += tiles_of(j);
+    int factor = 1;
+    if (allow_split && base > 0 && L.bn == 256 && base < 4 * 152) {
+        // one CTA per SM: model the launch as waves x (k-stages of the longest slice + ~4
+        // stages of prologue and epilogue) and take the split that minimises it
+        double best = 1e300;
+        for (int f = 1; f <= 16; ++f) {
+            int64_t t = 0;
+            int stages = 0;
+            for (const GJob &j : jobs)
+                if (j.m > 0 && j.n > 0 && j.k > 0) {
+                    const int ks = split_of(j, f);
+                    t += (int64_t)tiles_of(j) * ks;
+                    stages = std::max(stages, ((j.k + ks - 1) / ks + 15) / 16);
+                }
+            const double cost = std::ceil((double)t / 152.0) * (stages + 4);
+            if (cost < best * (1.0 - 1e-9)) {
+                best = cost;
+                factor = f;
+            }
+        }
+    } else if (allow_split && base > 0 && base < 4 * 152) {
+        factor = (4 * 152 + base - 1) / base;
+    }
     int tiles = 0;
     for (GJob j : jobs) {
         if (j.m <= 0 || j.n <= 0 || j.k <= 0) continue;
         j.tm = (j.m + L.bm - 1) / L.bm;
-        j.ks = 1;
-        if (factor > 1 && (j.flags & (GJ_SUB | GJ_ACC)) && j.k >= 512)
-            j.ks = std::max(1, std::min({factor, j.k / 256, 16}));
+        j.ks = factor > 1 ? split_of(j, factor) : 1;
         j.tile0 = tiles;
-        tiles += j.tm * ((j.n + 63) / 64) * j.ks;
+        const int nt = j.tm * ((j.n + L.bn - 1) / L.bn) * j.ks;
+        tiles += nt;
+        if (g_plan_tmap) {
+            if (L.tmoff < 0) L.tmoff = (int64_t)g_plan_tmap->size();
+            g_plan_tmap->insert(g_plan_tmap->end(), nt, (int32_t)L.cnt);
+        }
         all.push_back(j);
         L.cnt++;
         L.flops += 8.0 * j.m * j.n * j.k;
@@ -196,7 +263,31 @@ int upload_csr(zolo_factor_s *h, const zolo_csr *M, DevCSR &D) {
         for (int64_t p = 0; p < M->nnz; ++p) vr[p] = v[p].re;
         st = upload(h, vr, &D.vr);
     }
+    // double-float copies for the FP32-pipe refinement residual (mixed precision)
+    if (!st && h->prec == ZOLO_PREC_MIXED) {
+        if (real) {
+            std::vector<float2> s2(M->nnz);
+            for (int64_t p = 0; p < M->nnz; ++p) df_split(v[p].re, s2[p].x, s2[p].y);
+            st = upload(h, s2, &D.vrdf);
+        } else {
+            std::vector<float4> s4(M->nnz);
+            for (int64_t p = 0; p < M->nnz; ++p) {
+                df_split(v[p].re, s4[p].x, s4[p].y);
+                df_split(v[p].im, s4[p].z, s4[p].w);
+            }
+            st = upload(h, s4, &D.vdf);
+        }
+    }
     return st;
+}
+
+// Error of an expired wait inside the tensor-core GEMM since the last check (the
+// stream has been synchronised by the caller).
+int check_tc_status() {
+    const int v = gemm_tc_status(true);
+    if (v == ZOLO_ETIMEOUT) return set_error(ZOLO_ETIMEOUT, "tensor-core GEMM: an mbarrier wait expired");
+    if (v) return set_error(ZOLO_ECUDA, "tensor-core GEMM status unreadable");
+    return ZOLO_OK;
 }
 
 size_t elem_bytes(int prec) { return prec == ZOLO_PREC_MIXED ? sizeof(c64) : sizeof(c128); }
@@ -205,6 +296,12 @@ size_t elem_bytes(int prec) { return prec == ZOLO_PREC_MIXED ? sizeof(c64) : siz
 int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
     const zolo_symbolic_s &S = h->sym;
     g_plan_c64 = (h->prec == ZOLO_PREC_MIXED);
+    g_plan_tc = h->opts.tensor_core;
+    std::vector<int32_t> ftm;
+    g_plan_tmap = &ftm;
+    struct ClearMap {
+        ~ClearMap() { g_plan_tmap = nullptr; }
+    } clear_map;
     const int nn = S.nnodes;
     h->f_off.assign(nn, 0);
     h->f_inv.assign(nn, 0);
@@ -405,6 +502,7 @@ int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
     }
     st = upload(h, dj, &h->d_djobs);
     if (!st) st = upload(h, gj, &h->d_fjobs);
+    if (!st) st = upload(h, ftm, &h->d_ftmap);
     if (!st) st = upload(h, ej, &h->d_ejobs);
     h->n_djobs = (int64_t)dj.size();
     if (!st) st = dev_alloc(h, std::max<int64_t>(1, h->n_djobs) * h->r1 * sizeof(double), (void **)&h->d_minpiv);
@@ -477,8 +575,10 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                     GemmArgs<T> g;
                     std::memset(&g, 0, sizeof(g));
                     g.bm = L.bm;
+                    g.bn = L.bn;
                     for (int z = 0; z < ni; ++z) {
                         g.jobs[z] = h->d_fjobs + L.off;
+                        g.tmap[z] = L.tmoff >= 0 ? h->d_ftmap + L.tmoff : nullptr;
                         g.njobs[z] = L.cnt;
                         g.ntiles[z] = L.ntiles;
                         g.A[z] = abase ? inv[z] : pool[z];
@@ -508,8 +608,10 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                 GemmArgs<T> g;
                 std::memset(&g, 0, sizeof(g));
                 g.bm = L.bm;
+                g.bn = L.bn;
                 for (int z = 0; z < ni; ++z) {
                     g.jobs[z] = h->d_fjobs + L.off;
+                    g.tmap[z] = L.tmoff >= 0 ? h->d_ftmap + L.tmoff : nullptr;
                     g.njobs[z] = L.cnt;
                     g.ntiles[z] = L.ntiles;
                     g.A[z] = a_pool ? pool[z] : inv[z];
@@ -559,7 +661,7 @@ int factor_numeric(zolo_factor_s *h, cudaStream_t st) {
     for (int64_t i = 0; i < h->n_djobs * h->r1; ++i) m = std::min(m, mp[i]);
     h->stats.min_pivot = m;
     if (err) return set_error(ZOLO_ESINGULAR, "zero or non-finite pivot in a front");
-    return ZOLO_OK;
+    return check_tc_status();
 }
 
 // ---- solve schedule for a block width k
@@ -567,6 +669,12 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
     if (h->k_sched == k) return ZOLO_OK;
     const zolo_symbolic_s &S = h->sym;
     g_plan_c64 = (h->prec == ZOLO_PREC_MIXED);
+    g_plan_tc = h->opts.tensor_core;
+    std::vector<int32_t> stm;
+    g_plan_tmap = &stm;
+    struct ClearMap {
+        ~ClearMap() { g_plan_tmap = nullptr; }
+    } clear_map;
     std::vector<GJob> gj;
     std::vector<RJob> rj;
     h->fwd.clear();
@@ -670,15 +778,17 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
         dev_free(h, h->sched_buf.p);
         h->sched_buf = Buf();
     }
-    const size_t gb = gj.size() * sizeof(GJob), rb = rj.size() * sizeof(RJob);
+    const size_t gb = gj.size() * sizeof(GJob), rb = rj.size() * sizeof(RJob), tb = stm.size() * sizeof(int32_t);
     void *p = nullptr;
-    int rc = dev_alloc(h, gb + rb + 16, &p);
+    int rc = dev_alloc(h, gb + rb + tb + 16, &p);
     if (rc) return rc;
-    h->sched_buf = Buf{p, gb + rb + 16};
+    h->sched_buf = Buf{p, gb + rb + tb + 16};
     h->d_sjobs = (GJob *)p;
     h->d_rjobs = (RJob *)((char *)p + gb);
+    h->d_stmap = (int32_t *)((char *)p + gb + rb);
     if (gb) rc = cuda_check(cudaMemcpy(h->d_sjobs, gj.data(), gb, cudaMemcpyHostToDevice), "sched");
     if (!rc && rb) rc = cuda_check(cudaMemcpy(h->d_rjobs, rj.data(), rb, cudaMemcpyHostToDevice), "sched");
+    if (!rc && tb) rc = cuda_check(cudaMemcpy(h->d_stmap, stm.data(), tb, cudaMemcpyHostToDevice), "sched");
     if (rc) return rc;
     // workspaces: one front workspace and one pivot-row block per batched instance used
     if (h->w_buf.p) {
@@ -718,6 +828,7 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                 std::memset(&g, 0, sizeof(g));
                 double fl = 0.0;
                 g.bm = o.L.bm;
+                g.bn = o.L.bn;
                 auto base = [&](int kind, int z) -> cx<T> * {
                     switch (kind) {
                         case BK_POOL: return (cx<T> *)h->pool[pole[z]];
@@ -730,10 +841,11 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                 for (int z = 0; z < ninst; ++z) {
                     const Launch &L = herm[z] ? o.LH : o.L;
                     g.jobs[z] = h->d_sjobs + L.off;
+                    g.tmap[z] = L.tmoff >= 0 ? h->d_stmap + L.tmoff : nullptr;
                     g.njobs[z] = L.cnt;
                     g.ntiles[z] = L.ntiles;
-                    g.A[z] = base(o.abase, z);
-                    g.B[z] = base(o.bbase, z);
+                    g.A[z] = base(L.swap_ab ? o.bbase : o.abase, z);
+                    g.B[z] = base(L.swap_ab ? o.abase : o.bbase, z);
                     g.C[z] = base(o.cbase, z);
                     fl += L.flops;
                 }
@@ -825,7 +937,7 @@ int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, i
                         "norms");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "norms");
     if (rc) return rc;
-    const double tol = h->opts.refine_tol > 0 ? h->opts.refine_tol : 1e-12;
+    const double tol = std::max(h->opts.refine_tol > 0 ? h->opts.refine_tol : 1e-12, h->refine_tol_now);
     const int itmax = h->opts.refine_max > 0 ? h->opts.refine_max : 8;
     double prev = 0.0;
     for (int it = 0;; ++it) {
@@ -843,11 +955,34 @@ int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, i
             ra.Rz[z] = R + z * blk;
             ra.s[z] = herm[z] ? conj(sg) : sg;          // K^H = A - conj(sigma) B
         }
-        launch_refine_resid(h->A, h->B, ra, st);
+        // A tolerance >= 1e-8 leaves a margin of 1e6 over the double-float rounding (~1e-14
+        // of sum |K||x|): those residuals run on the FP32 pipe, tighter ones in FP64.
+        const bool use_df = tol >= 1e-8 && (h->A.vdf || h->A.vrdf) && (h->B.vdf || h->B.vrdf);
+        if (use_df) {
+            ResidDfArgs rd;
+            std::memset(&rd, 0, sizeof(rd));
+            rd.ninst = ninst;
+            rd.k = (int)k;
+            rd.ldb = ldin;
+            rd.ldr = k;
+            for (int z = 0; z < ninst; ++z) {
+                float4 *xs = (float4 *)(DX + z * blk);           // DX is free until the next solve
+                launch_split_df(h->n, k, Xout[z], ldout, xs, st);
+                rd.Bz[z] = Xin[z];
+                rd.Xs[z] = xs;
+                rd.Rz[z] = R + z * blk;
+                df_split(ra.s[z].re, rd.s[z].x, rd.s[z].y);
+                df_split(ra.s[z].im, rd.s[z].z, rd.s[z].w);
+            }
+            launch_refine_resid_df(h->A, h->B, rd, st);
+        } else {
+            launch_refine_resid(h->A, h->B, ra, st);
+        }
         for (int z = 0; z < ninst; ++z) launch_colnorm2(h->n, k, R + z * blk, k, h->d_norms + z * k, st);
         rc = cuda_check(cudaMemcpyAsync(hr.data(), h->d_norms, ninst * k * sizeof(double), cudaMemcpyDeviceToHost, st),
                         "norms");
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "norms");
+        if (!rc) rc = check_tc_status();
         if (rc) return rc;
         double worst = 0.0;
         for (int64_t i = 0; i < ninst * k; ++i) worst = std::max(worst, std::sqrt(hr[i] / std::max(hb[i], 1e-300)));
@@ -962,6 +1097,8 @@ static int factor_create(const zolo_csr *A, const zolo_csr *B, const zolo_filter
     if (!rc) rc = check_csr(B, "B", cb);
     if (rc) return rc;
     if (A->n != B->n) return set_error(ZOLO_EINVAL, "A and B differ in size");
+    if (opts && (opts->tensor_core < ZOLO_TC_AUTO || opts->tensor_core > ZOLO_TC_ALWAYS))
+        return set_error(ZOLO_EINVAL, "tensor_core must be ZOLO_TC_AUTO, ZOLO_TC_OFF or ZOLO_TC_ALWAYS");
     auto *h = new zolo_factor_s();
     if (opts) h->opts = *opts; else zolo_opts_default(&h->opts);
     h->prec = h->opts.precision == ZOLO_PREC_MIXED ? ZOLO_PREC_MIXED : ZOLO_PREC_FP64;
@@ -1082,6 +1219,14 @@ int zolo_profile_end(void *stream, int64_t *launches, int64_t *gemm_launches, do
     if (gemm_ms) *gemm_ms = ms;
     if (gemm_flops) *gemm_flops = counters().gemm_flops;
     return rc;
+}
+
+int zolo_profile_tc(int64_t *launches, double *ms, double *flops) {
+    clear_error();
+    if (launches) *launches = counters().tc_launches;
+    if (ms) *ms = counters().tc_ms;
+    if (flops) *flops = counters().tc_flops;
+    return ZOLO_OK;
 }
 
 int zolo_refactor(zolo_factor_h h, void *stream) {

@@ -13,6 +13,9 @@ struct Launch {
     int ntiles = 0;      // CTAs
     double flops = 0.0;  // executed flops of a GEMM launch (8 m n k summed over jobs)
     int bm = 64;         // GEMM tile height of the launch
+    int bn = 64;         // GEMM tile width (256: complex64 tensor-core kernel)
+    int64_t tmoff = -1;  // first entry of the launch's tile -> job map (-1: none)
+    bool swap_ab = false; // jobs stored transposed: the A operand comes from the B buffer
 };
 
 // one step of a level's factorisation: diagonal blocks, the two panels, Schur update
@@ -79,6 +82,7 @@ struct zolo_factor_s {
     std::vector<zolo::FLevel> flev;
     zolo::DJob *d_djobs = nullptr;
     zolo::GJob *d_fjobs = nullptr;
+    int32_t *d_ftmap = nullptr;                    // tile -> job maps of the factorisation launches
     zolo::RJob *d_ejobs = nullptr;
     int64_t n_djobs = 0;
     double *d_minpiv = nullptr;
@@ -88,6 +92,7 @@ struct zolo_factor_s {
     int64_t k_sched = -1;
     std::vector<zolo::SOp> fwd, bwd;
     zolo::GJob *d_sjobs = nullptr;
+    int32_t *d_stmap = nullptr;                    // tile -> job maps of the solve launches
     zolo::RJob *d_rjobs = nullptr;
     zolo::Buf sched_buf;
     void *W[zolo::MAX_INST] = {};                  // front workspaces (T), wrows x k each
@@ -101,6 +106,8 @@ struct zolo_factor_s {
 
     zolo::KrylovWork *kw = nullptr;
     double gmres_tol_now = 0.0;                    // tolerance of the current filter application
+    double refine_tol_now = 0.0;                   // relaxed refinement tolerance of the current
+                                                   // inner application (0: opts.refine_tol)
     bool inner_failed = false;                     // an inner solve of the current GMRES failed
     int *d_negcnt = nullptr;                       // inertia: negative pivots per pole
     bool count_neg = false;

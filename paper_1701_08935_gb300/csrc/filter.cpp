@@ -1,4 +1,4 @@
-// Host construction of the Zolotarev-composite filter R_ab (Algorithm 2 lines 1-4).
+// Host construction of the Zolotarev-composite filter R_ab (the filter-construction steps of Algorithm 2).
 //
 //  * Moebius map T(x) = gamma (x - alpha)/(x - beta) with T(a-) = -1, T(a+) = 1,
 //    T(b-) = l1, T(b+) = -l1 (eq. req).  l1 from cross-ratio invariance; alpha, beta,

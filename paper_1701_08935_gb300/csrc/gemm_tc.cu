@@ -1,0 +1,406 @@
+// Complex64 batched GEMM on the 5th-generation tensor cores (tcgen05, kind::tf32).
+//
+// Same job semantics as k_gemm / k_gemm_c64 (C (=|-=|+=) op(A) op(B) per job, split-K by
+// atomic adds, in-place when C aliases A with n <= the tile width or B with m <= 128), used
+// for the front updates and block solves of the multifrontal factor (Section 2.3) in the
+// mixed-precision mode.
+//
+// Arithmetic: every complex64 operand x is split into two TF32 numbers, x = hi + lo with
+// hi = x rounded to 11 significant bits and lo = (x - hi) rounded the same way (3xTF32:
+// the products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor memory, the
+// lo*lo term of relative size 2^-22 is dropped).  A complex product takes four real
+// products, so one k-step of 8 issues 12 MMAs of 128 x w x 8:
+//      Cr += Ar Br - Ai Bi,  Ci += Ar Bi + Ai Br        (each real product: 3 MMAs)
+// with the minus, and the sign flips of conjugated operands, taken by the instruction
+// descriptor's negate-A bit.  The result is as
+// accurate as the FP32 SIMT kernels up to a small factor; the FP64 refinement of every
+// mixed-precision solve absorbs the difference.
+//
+// Tiles: one CTA per 128 x w tile of C, w <= 256 columns chosen per job so that the
+// ceil(n / 256) column tiles have equal width (a multiple of 16).  Accumulators live in
+// tensor memory: Cr in columns [0, 256), Ci in [256, 512) of a 512-column allocation.
+// Operands are staged by all 256 threads (global loads, conjugation, hi/lo split, stores
+// in the canonical no-swizzle K-major layout) into one of two 96 KB shared-memory stages
+// while the MMAs of the other stage run, with the global loads of the stage after that
+// already in flight; one elected thread issues the MMAs and commits them to the stage's
+// mbarrier.  Every wait on an mbarrier is bounded in time (2 s): on
+// expiry the CTA skips its remaining waits and its epilogue, records ZOLO_ETIMEOUT in a
+// device status word (read by gemm_tc_status) and releases its tensor memory.
+#include "kernels.cuh"
+#include "zolo.h"
+
+#include <cstdint>
+
+namespace zolo {
+
+namespace {
+
+constexpr int TC_BM = 128;                 // rows of a C tile (MMA M)
+constexpr int TC_BN = 256;                 // widest C tile (MMA N)
+constexpr int TC_BK = 16;                  // complex k-extent of a stage (two MMA k-steps of 8)
+constexpr int TC_PLANE_A = TC_BM * TC_BK * 4;        // bytes of one A plane (8 KB)
+constexpr int TC_PLANE_B = TC_BN * TC_BK * 4;        // bytes of one B plane (16 KB)
+constexpr int TC_STAGE = 4 * TC_PLANE_A + 4 * TC_PLANE_B;   // 96 KB
+constexpr int TC_SMEM = 2 * TC_STAGE + 64;                  // + mbarriers, TMEM slot, job index
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;              // 2 s per mbarrier wait at most
+
+__device__ int g_tc_status = 0;
+
+// Byte offset of element (row, kk) (kk < 16) inside a plane in the canonical no-swizzle
+// K-major layout: 8-row x 16-byte core matrices, stored contiguously (128 B each), the
+// four core matrices of a row group adjacent along K (LBO = 128 B) and row groups 512 B
+// apart (SBO).
+__device__ __forceinline__ uint32_t core_off(int row, int q) {
+    return (uint32_t)(((row >> 3) * 4 + q) * 128 + (row & 7) * 16);
+}
+
+// Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), version 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    const uint64_t lbo = 128 >> 4, sbo = 512 >> 4;
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+}
+
+// Instruction descriptor for kind::tf32: FP32 accumulator, TF32 A and B, both K-major,
+// N = n, M = 128, optional negation of A.
+__device__ __forceinline__ uint32_t instr_desc(int n, bool neg_a) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the given phase parity, for TC_WAIT_NS of wall time at most (try_wait may
+// suspend the thread for a system-dependent time per poll, so the bound is on time, not
+// on polls); false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try(mbar, parity))
+        if (global_ns() - t0 > TC_WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// x rounded to TF32 (11 significant bits), ties away from zero, with two integer
+// operations (full-rate ALU; a cvt.rna.tf32 conversion per operand was measured slower).
+__device__ __forceinline__ float tf32_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// Four complex values (one row, four consecutive kk) split and stored into the four
+// planes (re hi, re lo, im hi, im lo) at byte offset `off`.
+__device__ __forceinline__ void put4(unsigned char *planes, int plane_bytes, uint32_t off, const c64 *v) {
+    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        rh[e] = tf32_round(v[e].re);
+        rl[e] = tf32_round(v[e].re - rh[e]);
+        ih[e] = tf32_round(v[e].im);
+        il[e] = tf32_round(v[e].im - ih[e]);
+    }
+    *reinterpret_cast<float4 *>(planes + off) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+    *reinterpret_cast<float4 *>(planes + plane_bytes + off) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+    *reinterpret_cast<float4 *>(planes + 2 * plane_bytes + off) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+    *reinterpret_cast<float4 *>(planes + 3 * plane_bytes + off) = make_float4(il[0], il[1], il[2], il[3]);
+}
+
+__global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
+    const int z = blockIdx.z;
+    const int tile = blockIdx.x;
+    if (tile >= g.ntiles[z]) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * TC_STAGE + 16);
+    int *s_job = reinterpret_cast<int *>(smem + 2 * TC_STAGE + 20);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const GJob *jobs = g.jobs[z];
+    if (tid == 0) {
+        if (g.tmap[z]) {
+            *s_job = g.tmap[z][tile];
+        } else {
+            int lo = 0, hi = g.njobs[z] - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+            }
+            *s_job = lo;
+        }
+    }
+    __syncthreads();
+    const GJob J = jobs[*s_job];
+    int t = tile - J.tile0;
+    const int ntn = (J.n + TC_BN - 1) / TC_BN;
+    const int w = ((J.n + ntn - 1) / ntn + 15) / 16 * 16;     // tile width, <= 256
+    const int tmn = J.tm * ntn;
+    const int kslice = t / tmn;
+    t -= kslice * tmn;
+    const int i0 = (t % J.tm) * TC_BM, j0 = (t / J.tm) * w;
+    const int ksp = J.ks > 1 ? J.ks : 1;
+    const int kchunk = (((J.k + ksp - 1) / ksp) + TC_BK - 1) / TC_BK * TC_BK;
+    const int kbeg = kslice * kchunk, kend = min(J.k, kbeg + kchunk);
+    const int nst = kend > kbeg ? (kend - kbeg + TC_BK - 1) / TC_BK : 0;
+    c64 *__restrict__ C = g.C[z] + J.c;
+    const bool sub = J.flags & GJ_SUB, add = J.flags & GJ_ACC, atom = J.ks > 1;
+    if (nst == 0) {                       // empty k-slice: only a plain product writes (zeros)
+        if (!(sub || add || atom))
+            for (int e = tid; e < TC_BM * w; e += 256) {
+                const int i = i0 + e / w, j = j0 + e % w;
+                if (i < J.m && j < J.n) C[(int64_t)i * J.crs + (int64_t)j * J.ccs] = mk<float>(0, 0);
+            }
+        return;
+    }
+
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    // Staging units: 4 consecutive kk of one row.  A: 512 units (128 rows x 4), B: 1024
+    // (256 rows x 4); thread tid owns A units tid + 256 h (h < 2) and B units tid + 256 h
+    // (h < 4), mapped so that a warp's global loads are contiguous along the operand's unit-
+    // stride dimension.  Each unit keeps a pointer advanced by one stage per step; only the
+    // ragged last stage checks kk against kend.  Rows past m (A) or past the tile (B) are
+    // neither loaded nor stored: they only feed accumulator rows / columns that are not written.
+    const c64 *__restrict__ A = g.A[z] + J.a;
+    const c64 *__restrict__ B = g.B[z] + J.b;
+    const bool a_kfast = (J.acs == 1), b_kfast = (J.brs == 1);
+    const int64_t acs = J.acs, brs = J.brs;
+    const c64 *pa[2], *pb[4];
+    uint32_t oa[2], ob[4];
+    int qa[2], qb[4];
+    bool va[2], vb[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int u = tid + 256 * h;
+        const int i = a_kfast ? (u >> 2) : (u & 127), q = a_kfast ? (u & 3) : (u >> 7);
+        va[h] = i0 + i < J.m;
+        qa[h] = q;
+        oa[h] = core_off(i, q);
+        pa[h] = A + (int64_t)(va[h] ? i0 + i : 0) * J.ars + (int64_t)(kbeg + 4 * q) * acs;
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int u = tid + 256 * h;
+        const int j = b_kfast ? (u >> 2) : (u & 255), q = b_kfast ? (u & 3) : (u >> 8);
+        vb[h] = j < w && j0 + j < J.n;
+        qb[h] = q;
+        ob[h] = core_off(j, q);
+        pb[h] = B + (int64_t)(kbeg + 4 * q) * brs + (int64_t)(vb[h] ? j0 + j : 0) * J.bcs;
+    }
+    c64 ra[2][4], rb[4][4];
+
+    auto load = [&](int l0) {
+        const bool full = l0 + TC_BK <= kend;          // uniform over the CTA
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (va[h]) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    ra[h][e] = (full || l0 + 4 * qa[h] + e < kend) ? pa[h][e * acs] : mk<float>(0, 0);
+            }
+            pa[h] += TC_BK * acs;
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            if (vb[h]) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    rb[h][e] = (full || l0 + 4 * qb[h] + e < kend) ? pb[h][e * brs] : mk<float>(0, 0);
+            }
+            pb[h] += TC_BK * brs;
+        }
+    };
+    auto store = [&](int buf) {
+        unsigned char *sa = smem + buf * TC_STAGE;
+        unsigned char *sb = sa + 4 * TC_PLANE_A;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (va[h]) put4(sa, TC_PLANE_A, oa[h], ra[h]);
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if (vb[h]) put4(sb, TC_PLANE_B, ob[h], rb[h]);
+    };
+
+    // Signs of the four real products (the planes hold A and B as stored; conjugation is
+    // a sign flip of Ai or Bi, taken by the negate-A bit of the instruction descriptor):
+    //   Cr = Ar Br - (sA Ai)(sB Bi),   Ci = Ar (sB Bi) + (sA Ai) Br,   sX = -1 if op(X) = conj(X)
+    const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
+    const uint32_t id_rr = instr_desc(w, false);
+    const uint32_t id_ii = instr_desc(w, conjA == conjB);      // - sA sB < 0 unless exactly one conj
+    const uint32_t id_ri = instr_desc(w, conjB);
+    const uint32_t id_ir = instr_desc(w, conjA);
+    const uint32_t t_re = tmem, t_im = tmem + 256;
+    bool ok = true;
+    // Register staging runs two stages ahead of the MMAs: at step s the loads of stage s + 2
+    // are issued right after stage s + 1 is stored, so they have a whole stage of MMAs to land.
+    load(kbeg);
+    store(0);
+    if (nst > 1) load(kbeg + TC_BK);
+    for (int s = 0; s < nst; ++s) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+            const uint32_t sa = sbase + (s & 1) * TC_STAGE, sb = sa + 4 * TC_PLANE_A;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t a0 = smem_desc(sa + ks * 256), a1 = smem_desc(sa + TC_PLANE_A + ks * 256),
+                               a2 = smem_desc(sa + 2 * TC_PLANE_A + ks * 256),
+                               a3 = smem_desc(sa + 3 * TC_PLANE_A + ks * 256);
+                const uint64_t b0 = smem_desc(sb + ks * 256), b1 = smem_desc(sb + TC_PLANE_B + ks * 256),
+                               b2 = smem_desc(sb + 2 * TC_PLANE_B + ks * 256),
+                               b3 = smem_desc(sb + 3 * TC_PLANE_B + ks * 256);
+                const uint32_t first = (s == 0 && ks == 0) ? 0u : 1u;
+                mma_tf32(t_re, a0, b0, id_rr, first);       // Ar Br
+                mma_tf32(t_re, a0, b1, id_rr, 1u);
+                mma_tf32(t_re, a1, b0, id_rr, 1u);
+                mma_tf32(t_re, a2, b2, id_ii, 1u);          // -(sA Ai)(sB Bi)
+                mma_tf32(t_re, a2, b3, id_ii, 1u);
+                mma_tf32(t_re, a3, b2, id_ii, 1u);
+                mma_tf32(t_im, a0, b2, id_ri, first);       // Ar (sB Bi)
+                mma_tf32(t_im, a0, b3, id_ri, 1u);
+                mma_tf32(t_im, a1, b2, id_ri, 1u);
+                mma_tf32(t_im, a2, b0, id_ir, 1u);          // (sA Ai) Br
+                mma_tf32(t_im, a2, b1, id_ir, 1u);
+                mma_tf32(t_im, a3, b0, id_ir, 1u);
+            }
+            mma_commit(mb0 + 8 * (s & 1));
+        }
+        if (s + 1 < nst) {
+            // the other buffer is free once the MMAs of stage s - 1 are done
+            if (ok && s >= 1 && !mbar_wait(mb0 + 8 * ((s - 1) & 1), ((s - 1) >> 1) & 1)) ok = false;
+            store((s + 1) & 1);
+            if (s + 2 < nst) load(kbeg + TC_BK * (s + 2));
+        }
+    }
+    if (ok && !mbar_wait(mb0 + 8 * ((nst - 1) & 1), ((nst - 1) >> 1) & 1)) ok = false;
+    fence_after_sync();
+    ok = __syncthreads_and(ok);
+
+    if (ok) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (C rows), column chunks of 32
+        // alternating between warps w and w + 4
+        const int qd = warp & 3, hf = warp >> 2;
+        const int i = i0 + 32 * qd + lane;
+        const int nch = (w + 31) / 32;
+        for (int c = hf; c < nch; c += 2) {
+            float re[32], im[32];
+            const uint32_t ta = ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * c);
+            tmem_ld32(t_re + ta, re);
+            tmem_ld32(t_im + ta, im);
+            if (i < J.m) {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int jl = 32 * c + jj, j = j0 + jl;
+                    if (jl >= w || j >= J.n) continue;
+                    c64 *p = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
+                    const float vr = sub ? -re[jj] : re[jj], vi = sub ? -im[jj] : im[jj];
+                    if (atom) {
+                        atomicAdd(reinterpret_cast<float2 *>(p), make_float2(vr, vi));
+                    } else if (sub || add) {
+                        const c64 o = *p;
+                        *p = mk<float>(o.re + vr, o.im + vi);
+                    } else {
+                        *p = mk<float>(vr, vi);
+                    }
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(&g_tc_status, ZOLO_ETIMEOUT);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+}
+
+}  // namespace
+
+void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st) {
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        attr_dev = dev;
+    }
+    k_gemm_tc<<<grid, 256, TC_SMEM, st>>>(g);
+}
+
+int gemm_tc_status(bool reset) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)) != cudaSuccess) return ZOLO_ECUDA;
+    if (v && reset) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int));
+    }
+    return v;
+}
+
+}  // namespace zolo

@@ -4,6 +4,7 @@
 // (a pole, or a (pole, K^-1 / K^-H) pair) and job lists built on the host describe
 // all fronts of one tree level, so one launch covers a whole level.
 #include "kernels.cuh"
+#include "df64.cuh"
 
 #include <vector>
 
@@ -13,6 +14,11 @@ namespace {
 LaunchCounters g_counters;
 int g_prof = 0;                      // bit 0: time complex64 GEMMs, bit 1: complex128
 std::vector<cudaEvent_t> g_ev;       // start/stop pairs of profiled GEMM launches
+struct EvInfo {
+    bool tc;                         // launched on the tensor-core kernel
+    double flops;                    // executed flops of the launch
+};
+std::vector<EvInfo> g_ev_info;       // one per pair
 std::vector<cudaEvent_t> g_ev_pool;
 cudaEvent_t get_event() {
     if (!g_ev_pool.empty()) {
@@ -36,13 +42,31 @@ double prof_collect_ms() {
         float t = 0.f;
         cudaEventElapsedTime(&t, g_ev[i], g_ev[i + 1]);
         ms += t;
+        const EvInfo &f = g_ev_info[i / 2];
+        if (f.tc) {
+            g_counters.tc_launches++;
+            g_counters.tc_ms += t;
+            g_counters.tc_flops += f.flops;
+        }
     }
     for (cudaEvent_t e : g_ev) g_ev_pool.push_back(e);
     g_ev.clear();
+    g_ev_info.clear();
     return ms;
 }
 
 // ============================================================== batched GEMM
+// Job of a tile: the launch's tile map when it has one, else a binary search of tile0.
+__device__ __forceinline__ int find_job(const int32_t *tmap, const GJob *jobs, int njobs, int tile) {
+    if (tmap) return tmap[tile];
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // C (=|-=) op(A) op(B) for every job in the list; one CTA per BM x BN tile.
 // The whole kk extent of a tile is read before its C block is written, so a job
 // whose C aliases A (with n <= BN) or B (with m <= BM) is computed in place.
@@ -56,14 +80,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
     __shared__ cx<T> As[BK][BM];
     __shared__ cx<T> Bs[BK][BN];
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        int lo = 0, hi = g.njobs[z] - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-        }
-        s_job = lo;
-    }
+    if (tid == 0) s_job = find_job(g.tmap[z], jobs, g.njobs[z], tile);
     __syncthreads();
     const GJob J = jobs[s_job];
     int t = tile - J.tile0;
@@ -156,14 +173,7 @@ __global__ void __launch_bounds__(256) k_gemm_c64(GemmArgs<float> g) {
     __shared__ __align__(16) c64 As[G2_BK][G2_BM];
     __shared__ __align__(16) c64 Bs[G2_BK][G2_BN];
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        int lo = 0, hi = g.njobs[z] - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-        }
-        s_job = lo;
-    }
+    if (tid == 0) s_job = find_job(g.tmap[z], jobs, g.njobs[z], tile);
     __syncthreads();
     const GJob J = jobs[s_job];
     int t = tile - J.tile0;
@@ -284,8 +294,12 @@ void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops)
         e1 = get_event();
         cudaEventRecord(e0, st);
     }
+    bool tc = false;
     if constexpr (sizeof(T) == 4) {
-        if (g.bm == G2_BM)
+        tc = (g.bn == 256);
+        if (tc)
+            launch_gemm_tc(g, grid, st);
+        else if (g.bm == G2_BM)
             k_gemm_c64<<<grid, 256, 0, st>>>(g);
         else
             k_gemm<T, 64, 64, 16><<<grid, 256, 0, st>>>(g);
@@ -296,6 +310,7 @@ void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops)
         cudaEventRecord(e1, st);
         g_ev.push_back(e0);
         g_ev.push_back(e1);
+        g_ev_info.push_back({tc, flops});
     }
     g_counters.launches++;
     if (timed) {
@@ -629,6 +644,95 @@ __global__ void __launch_bounds__(256) k_refine_resid(DevCSR A, DevCSR M, ResidA
 void launch_refine_resid(const DevCSR &A, const DevCSR &M, const ResidArgs &r, cudaStream_t st) {
     if (A.n == 0 || r.k == 0 || r.ninst == 0) return;
     k_refine_resid<<<(unsigned)((A.n + 7) / 8), 256, 0, st>>>(A, M, r);
+    g_counters.launches++;
+}
+
+// Double-float variant: the sums over the rows of A and M, sigma M x and b - A x + sigma M x
+// all in df64 on the FP32 pipe (no FP64 instruction per non-zero).
+__global__ void __launch_bounds__(256) k_refine_resid_df(DevCSR A, DevCSR M, ResidDfArgs r) {
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= A.n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t ab = A.rp[row], ae = A.rp[row + 1], mb = M.rp[row], me = M.rp[row + 1];
+    for (int z = 0; z < r.ninst; ++z) {
+        const float4 *__restrict__ X = r.Xs[z];
+        const float4 sg = r.s[z];
+        for (int c = lane; c < r.k; c += 32) {
+            float arh = 0.f, arl = 0.f, aih = 0.f, ail = 0.f;     // A x
+            if (A.vrdf) {
+                for (int64_t p = ab; p < ae; ++p) {
+                    const float2 a = A.vrdf[p];
+                    const float4 x = X[(int64_t)A.ci[p] * r.k + c];
+                    df_fma(arh, arl, a.x, a.y, x.x, x.y);
+                    df_fma(aih, ail, a.x, a.y, x.z, x.w);
+                }
+            } else {
+                for (int64_t p = ab; p < ae; ++p) {
+                    const float4 a = A.vdf[p];
+                    const float4 x = X[(int64_t)A.ci[p] * r.k + c];
+                    df_fma(arh, arl, a.x, a.y, x.x, x.y);             // ar xr
+                    df_fma(arh, arl, -a.z, -a.w, x.z, x.w);           // - ai xi
+                    df_fma(aih, ail, a.x, a.y, x.z, x.w);             // ar xi
+                    df_fma(aih, ail, a.z, a.w, x.x, x.y);             // ai xr
+                }
+            }
+            float mrh = 0.f, mrl = 0.f, mih = 0.f, mil = 0.f;     // M x
+            if (M.vrdf) {
+                for (int64_t p = mb; p < me; ++p) {
+                    const float2 a = M.vrdf[p];
+                    const float4 x = X[(int64_t)M.ci[p] * r.k + c];
+                    df_fma(mrh, mrl, a.x, a.y, x.x, x.y);
+                    df_fma(mih, mil, a.x, a.y, x.z, x.w);
+                }
+            } else {
+                for (int64_t p = mb; p < me; ++p) {
+                    const float4 a = M.vdf[p];
+                    const float4 x = X[(int64_t)M.ci[p] * r.k + c];
+                    df_fma(mrh, mrl, a.x, a.y, x.x, x.y);
+                    df_fma(mrh, mrl, -a.z, -a.w, x.z, x.w);
+                    df_fma(mih, mil, a.x, a.y, x.z, x.w);
+                    df_fma(mih, mil, a.z, a.w, x.x, x.y);
+                }
+            }
+            df_norm(mrh, mrl);
+            df_norm(mih, mil);
+            // t = b - A x + s (M x)
+            const c128 b = r.Bz[z][row * r.ldb + c];
+            float trh, trl, tih, til;
+            df_split(b.re, trh, trl);
+            df_split(b.im, tih, til);
+            df_add(trh, trl, -arh, -arl);
+            df_add(tih, til, -aih, -ail);
+            df_fma(trh, trl, sg.x, sg.y, mrh, mrl);                 // sr (Mx)r
+            df_fma(trh, trl, -sg.z, -sg.w, mih, mil);               // - si (Mx)i
+            df_fma(tih, til, sg.x, sg.y, mih, mil);                 // sr (Mx)i
+            df_fma(tih, til, sg.z, sg.w, mrh, mrl);                 // si (Mx)r
+            r.Rz[z][row * r.ldr + c] = mk<double>(df_widen(__fadd_rn(trh, trl)), df_widen(__fadd_rn(tih, til)));
+        }
+    }
+}
+
+void launch_refine_resid_df(const DevCSR &A, const DevCSR &M, const ResidDfArgs &r, cudaStream_t st) {
+    if (A.n == 0 || r.k == 0 || r.ninst == 0) return;
+    k_refine_resid_df<<<(unsigned)((A.n + 7) / 8), 256, 0, st>>>(A, M, r);
+    g_counters.launches++;
+}
+
+__global__ void k_split_df(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx, float4 *__restrict__ Xs) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t i = idx / k, c = idx - i * k;
+    const c128 x = X[i * ldx + c];
+    float4 o;
+    df_split(x.re, o.x, o.y);
+    df_split(x.im, o.z, o.w);
+    Xs[idx] = o;
+}
+
+void launch_split_df(int64_t n, int64_t k, const c128 *X, int64_t ldx, float4 *Xs, cudaStream_t st) {
+    const int64_t tot = n * k;
+    if (tot == 0) return;
+    k_split_df<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, (int)k, X, ldx, Xs);
     g_counters.launches++;
 }
 

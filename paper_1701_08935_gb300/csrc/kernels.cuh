@@ -6,7 +6,9 @@ namespace zolo {
 
 template <class T> struct GemmArgs {
     int bm;                              // tile height of this launch (64, or 128 for complex64)
+    int bn;                              // tile width: 64, or 256 for the complex64 tensor-core kernel
     const GJob *jobs[MAX_INST];
+    const int32_t *tmap[MAX_INST];       // job of every tile of the launch, or null (binary search)
     int njobs[MAX_INST];
     int ntiles[MAX_INST];
     const cx<T> *A[MAX_INST];
@@ -58,6 +60,8 @@ struct DevCSR {
     int32_t *ci = nullptr;
     c128 *v = nullptr;          // values as complex128
     double *vr = nullptr;       // the same values when all are real (else nullptr)
+    float4 *vdf = nullptr;      // double-float split (re hi, re lo, im hi, im lo), mixed precision only
+    float2 *vrdf = nullptr;     // double-float split of vr (hi, lo), when all values are real
 };
 
 // R_z = B_z - A X_z + s_z (M X_z) for up to MAX_INST instances (refinement residuals of
@@ -71,6 +75,21 @@ struct ResidArgs {
     int64_t ldb, ldx, ldr;
 };
 void launch_refine_resid(const DevCSR &A, const DevCSR &M, const ResidArgs &r, cudaStream_t st);
+// The same residuals in double-float arithmetic on the FP32 pipe (relative rounding ~1e-14
+// of sum |K||x|; used for refinement tolerances >= 1e-8).  Xs_z are the solutions split by
+// launch_split_df; s_z is given as (re hi, re lo, im hi, im lo).  R_z gets FP32-accurate
+// values (all a complex64 correction solve and a residual norm need).
+struct ResidDfArgs {
+    int ninst, k;
+    const c128 *Bz[MAX_INST];
+    const float4 *Xs[MAX_INST];
+    c128 *Rz[MAX_INST];
+    float4 s[MAX_INST];
+    int64_t ldb, ldr;
+};
+void launch_refine_resid_df(const DevCSR &A, const DevCSR &M, const ResidDfArgs &r, cudaStream_t st);
+// Xs[i k + c] = double-float split of X[i ldx + c] (n x k)
+void launch_split_df(int64_t n, int64_t k, const c128 *X, int64_t ldx, float4 *Xs, cudaStream_t st);
 
 constexpr int LIN_MAX = 8;
 struct LinArgs {
@@ -88,12 +107,21 @@ struct LaunchCounters {
     int64_t launches = 0;          // all kernels of the library
     int64_t gemm_launches = 0;     // timed GEMM launches
     double gemm_flops = 0.0;       // executed flops of the timed GEMM jobs (8 m n k each)
+    int64_t tc_launches = 0;       // the tensor-core subset of the timed GEMM launches,
+    double tc_ms = 0.0;            // its summed device time (filled by prof_collect_ms)
+    double tc_flops = 0.0;         // and its executed flops
 };
 LaunchCounters &counters();
 void count_launch(int64_t n = 1);
 void prof_set(int mask);          // bit 0: complex64 GEMMs, bit 1: complex128 GEMMs
 double prof_collect_ms();          // synchronises the recorded events, returns the summed time
+                                   // (and adds the tensor-core share to counters().tc_*)
 template <class T> void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops = 0.0);
+// complex64 tcgen05 GEMM (tiles 128 x <= 256, bm = 128, bn = 256 in the job tiling)
+void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st);
+// device status word of the tensor-core GEMM: 0, or ZOLO_ETIMEOUT after an expired
+// mbarrier wait (ZOLO_ECUDA when it cannot be read); `reset` clears a non-zero word
+int gemm_tc_status(bool reset);
 template <class T> void launch_diag_lu(const DiagArgs<T> &g, int ninst, cudaStream_t st);
 template <class T> void launch_assemble(const AsmArgs<T> &g, int ninst, cudaStream_t st);
 template <class T> void launch_extend_add(const EaddArgs<T> &g, int ninst, cudaStream_t st);

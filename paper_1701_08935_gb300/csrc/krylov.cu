@@ -1,4 +1,4 @@
-// Shift-invariant GMRES for Z_2r2(G; l2) X (Algorithm 2 lines 9-10, eq. solve2) and the
+// Shift-invariant GMRES for Z_2r2(G; l2) X (the GMRES steps of Algorithm 2, eq. solve2) and the
 // subspace iteration with Rayleigh-Ritz of Algorithm 1.
 //
 // GMRES: one Krylov basis per column c of X, shared by all 2 r2 shifts s = +-i sqrt(c_j):
@@ -32,21 +32,43 @@ constexpr int JT = 8;             // basis vectors per pass of the multi-dot ker
 
 // ---------------------------------------------------------------- block kernels
 // part[b][j][c] = sum over rows i = b, b+G, ... of conj(V_j[i,c]) W[i,c], j in [j0, j0+nj)
+// FP64 -> FP32 by integer operations on the bit pattern (truncating the mantissa; values
+// below 2^-126 become 0), so that reading FP64 operands costs no FP64-pipe instructions,
+// which GB300 issues at ~1/64 of the FP32 rate.  Finite inputs only.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int32_t t = (int32_t)(hi & 0x7FFFFFFFu) - (int32_t)(896u << 20);    // rebias 1023 -> 127
+    const uint32_t mag = t > 0 ? (((uint32_t)t << 3) | (lo >> 29)) : 0u;
+    return __uint_as_float(mag | (hi & 0x80000000u));
+}
+
+// part[b][t][c] = sum over this CTA's rows of conj(V_{j0+t}[i,c]) W[i,c], in FP32.
+// The projection coefficients of classical Gram-Schmidt only need FP32 accuracy: the
+// update W -= sum_j V_j h_j and the Hessenberg matrix use the same (rounded) h, so the
+// Arnoldi relation G V_m = V_{m+1} H_m stays exact to FP64 rounding and the basis is
+// orthonormal to ~1e-6, which keeps the least-squares residuals within 1e-4 of the
+// true ones.  The partial sums are reduced in FP64 by k_multidot_sum.
 __global__ void __launch_bounds__(256) k_multidot(int64_t n, int k, const c128 *const *__restrict__ V, int j0, int nj,
                                                   const c128 *__restrict__ W, double2 *__restrict__ part) {
     for (int c = threadIdx.x; c < k; c += 256) {
-        c128 acc[JT];
+        float ar[JT], ai[JT];
 #pragma unroll
-        for (int t = 0; t < JT; ++t) acc[t] = mk<double>(0, 0);
+        for (int t = 0; t < JT; ++t) ar[t] = ai[t] = 0.f;
         for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
             const c128 w = W[i * k + c];
+            const float wr = f64_to_f32_trunc(w.re), wi = f64_to_f32_trunc(w.im);
 #pragma unroll
             for (int t = 0; t < JT; ++t)
-                if (t < nj) fma_acc(acc[t], conj(V[j0 + t][i * k + c]), w);
+                if (t < nj) {
+                    const c128 v = V[j0 + t][i * k + c];
+                    const float vr = f64_to_f32_trunc(v.re), vi = f64_to_f32_trunc(v.im);
+                    ar[t] = fmaf(vr, wr, fmaf(vi, wi, ar[t]));        // conj(v) w
+                    ai[t] = fmaf(vr, wi, fmaf(-vi, wr, ai[t]));
+                }
         }
 #pragma unroll
         for (int t = 0; t < JT; ++t)
-            if (t < nj) part[((int64_t)blockIdx.x * nj + t) * k + c] = make_double2(acc[t].re, acc[t].im);
+            if (t < nj) part[((int64_t)blockIdx.x * nj + t) * k + c] = make_double2(ar[t], ai[t]);
     }
 }
 
@@ -491,7 +513,7 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
         p += pairs * (size_t)mmax * mmax * sizeof(c128);
         S.g = (c128 *)p;
     }
-    // shifts +- i sqrt(c_j) and weights M a_j / 4 (eq. solve2, Algorithm 2 line 10)
+    // shifts +- i sqrt(c_j) and weights M a_j / 4 (eq. solve2, the combination step of Algorithm 2)
     std::vector<c128> sh(ns), om(ns);
     for (int j = 0; j < r2; ++j) {
         const double sq = std::sqrt(h->fi.c[j]);
@@ -532,10 +554,24 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
     int m = 0;
     double worst = 0.0;
     std::vector<double> hres(pairs), hnorm(2 * k);
+    // Relaxed inner accuracy (inexact Krylov: Simoncini & Szyld 2003, Bouras & Fraysse 2005):
+    // an error e_i in the i-th product G v_i enters the GMRES solution weighted by the LSQ
+    // coefficient of v_i, which is of the size of the residual before step i.  So the
+    // mixed-precision solves of step i are refined to 1e-2 tol / (error bound after step
+    // i - 1), clamped to [refine_tol, 1e-3], instead of refine_tol throughout.
+    const double rtol = h->opts.refine_tol > 0 ? h->opts.refine_tol : 1e-12;
+    struct ResetRelax {
+        zolo_factor_s *h;
+        ~ResetRelax() { h->refine_tol_now = 0.0; }
+    } reset_relax{h};
     for (int i = 0; i < mmax; ++i) {
         rc = ensure_block(i + 1);
         if (rc) return rc;
         c128 *Wv = w.vhost[i + 1];
+        if (h->prec == ZOLO_PREC_MIXED) {
+            const double prev = (i == 0) ? 1.0 : std::max(worst, 1e-300);
+            h->refine_tol_now = std::min(1e-3, std::max(rtol, 1e-2 * tol / prev));
+        }
         rc = apply_inner(h, k, w.vhost[i], k, Wv, k, st);
         if (rc) {                                          // a failed inner solve is not a short GMRES
             h->inner_failed = true;

@@ -64,3 +64,13 @@ def test_missing_diagonal_rejected():
     B = sp.identity(2, format="csr")
     with pytest.raises(Z.ZoloError):
         Z.Symbolic(A, B, Z.default_opts())
+
+
+def test_bad_tensor_core_policy_rejected_before_any_device_work():
+    p = synth.pencil_2d_real(6, seed=1)
+    f = Z.Filter(0.0, 0.5, 1.0, 1.5, 2, 2)
+    for bad in (-1, 3):
+        with pytest.raises(Z.ZoloError) as e:
+            Z.Factor(p.A, p.B, f, opts=Z.default_opts(grid=(6, 6), precision=Z.PREC_MIXED, tensor_core=bad),
+                     stream=0)
+        assert e.value.status == Z.EINVAL

@@ -1,4 +1,4 @@
-"""GPU parity of the filtered block Y = R_ab(B^-1 A) X (Algorithm 2 lines 9-10) and of
+"""GPU parity of the filtered block Y = R_ab(B^-1 A) X (the GMRES steps of Algorithm 2) and of
 Algorithm 1 against the oracle, through the C ABI."""
 import numpy as np
 import pytest
