@@ -102,39 +102,20 @@ constexpr double TC_MIN_ROWS = 128.0;
 Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool allow_split = false) {
     Launch L;
     L.off = (int64_t)all.size();
-    double msum = 0.0, nsum = 0.0;
+    double msum = 0.0;
     int cnt = 0;
     for (const GJob &j : jobs_in)
         if (j.m > 0 && j.n > 0 && j.k > 0) {
             msum += j.m;
-            nsum += j.n;
             ++cnt;
         }
-    // Short, wide products (a front's few pivot rows times a block of columns) fill the
-    // 128-row tensor-core tiles only when taken transposed: C^T = op(B)^T op(A)^T, a swap
-    // of operands, strides and conjugation flags.  Only solve launches (allow_split), whose
-    // C never aliases A or B, are transposed; the caller swaps the A and B base pointers.
-    std::vector<GJob> tj;
-    const std::vector<GJob> *src = &jobs_in;
-    if (g_plan_c64 && allow_split && cnt && g_plan_tc != ZOLO_TC_OFF && msum / cnt < TC_MIN_ROWS &&
-        nsum / cnt >= TC_MIN_ROWS) {
-        tj = jobs_in;
-        for (GJob &j : tj) {
-            std::swap(j.a, j.b);
-            const int ars = j.bcs, acs = j.brs, brs = j.acs, bcs = j.ars;
-            j.ars = ars; j.acs = acs; j.brs = brs; j.bcs = bcs;
-            std::swap(j.crs, j.ccs);
-            std::swap(j.m, j.n);
-            const int f = j.flags & ~(GJ_CONJA | GJ_CONJB);
-            j.flags = f | ((j.flags & GJ_CONJA) ? GJ_CONJB : 0) | ((j.flags & GJ_CONJB) ? GJ_CONJA : 0);
-        }
-        src = &tj;
-        L.swap_ab = true;
-        std::swap(msum, nsum);
-    }
-    const std::vector<GJob> &jobs = *src;
+    const std::vector<GJob> &jobs = jobs_in;
     const bool big = cnt && msum / cnt >= 256.0;
     L.bm = (g_plan_c64 && big) ? 128 : 64;
+    if (g_plan_c64 && cnt && msum / cnt <= 40.0) {       // few pivot rows: 32 x 128 FMA tiles
+        L.bm = 32;
+        L.bn = 128;
+    }
     if (g_plan_c64 && cnt &&
         (g_plan_tc == ZOLO_TC_ALWAYS || (g_plan_tc == ZOLO_TC_AUTO && msum / cnt >= TC_MIN_ROWS))) {
         L.bm = 128;
@@ -844,8 +825,8 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                     g.tmap[z] = L.tmoff >= 0 ? h->d_stmap + L.tmoff : nullptr;
                     g.njobs[z] = L.cnt;
                     g.ntiles[z] = L.ntiles;
-                    g.A[z] = base(L.swap_ab ? o.bbase : o.abase, z);
-                    g.B[z] = base(L.swap_ab ? o.abase : o.bbase, z);
+                    g.A[z] = base(o.abase, z);
+                    g.B[z] = base(o.bbase, z);
                     g.C[z] = base(o.cbase, z);
                     fl += L.flops;
                 }

@@ -15,7 +15,6 @@ struct Launch {
     int bm = 64;         // GEMM tile height of the launch
     int bn = 64;         // GEMM tile width (256: complex64 tensor-core kernel)
     int64_t tmoff = -1;  // first entry of the launch's tile -> job map (-1: none)
-    bool swap_ab = false; // jobs stored transposed: the A operand comes from the B buffer
 };
 
 // one step of a level's factorisation: diagonal blocks, the two panels, Schur update

@@ -11,8 +11,8 @@
 // lo*lo term of relative size 2^-22 is dropped).  A complex product takes four real
 // products, so one k-step of 8 issues 12 MMAs of 128 x w x 8:
 //      Cr += Ar Br - Ai Bi,  Ci += Ar Bi + Ai Br        (each real product: 3 MMAs)
-// with the minus, and the sign flips of conjugated operands, taken by the instruction
-// descriptor's negate-A bit.  The result is as
+// with the minus taken by the instruction descriptor's negate-A bit (conjugated operands
+// are conjugated while they are staged).  The result is as
 // accurate as the FP32 SIMT kernels up to a small factor; the FP64 refinement of every
 // mixed-precision solve absorbs the difference.
 //
@@ -219,80 +219,65 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    // Staging units: 4 consecutive kk of one row.  A: 512 units (128 rows x 4), B: 1024
-    // (256 rows x 4); thread tid owns A units tid + 256 h (h < 2) and B units tid + 256 h
-    // (h < 4), mapped so that a warp's global loads are contiguous along the operand's unit-
-    // stride dimension.  Each unit keeps a pointer advanced by one stage per step; only the
-    // ragged last stage checks kk against kend.  Rows past m (A) or past the tile (B) are
-    // neither loaded nor stored: they only feed accumulator rows / columns that are not written.
     const c64 *__restrict__ A = g.A[z] + J.a;
     const c64 *__restrict__ B = g.B[z] + J.b;
+    const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
     const bool a_kfast = (J.acs == 1), b_kfast = (J.brs == 1);
-    const int64_t acs = J.acs, brs = J.brs;
-    const c64 *pa[2], *pb[4];
-    uint32_t oa[2], ob[4];
-    int qa[2], qb[4];
-    bool va[2], vb[4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int u = tid + 256 * h;
-        const int i = a_kfast ? (u >> 2) : (u & 127), q = a_kfast ? (u & 3) : (u >> 7);
-        va[h] = i0 + i < J.m;
-        qa[h] = q;
-        oa[h] = core_off(i, q);
-        pa[h] = A + (int64_t)(va[h] ? i0 + i : 0) * J.ars + (int64_t)(kbeg + 4 * q) * acs;
-    }
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int u = tid + 256 * h;
-        const int j = b_kfast ? (u >> 2) : (u & 255), q = b_kfast ? (u & 3) : (u >> 8);
-        vb[h] = j < w && j0 + j < J.n;
-        qb[h] = q;
-        ob[h] = core_off(j, q);
-        pb[h] = B + (int64_t)(kbeg + 4 * q) * brs + (int64_t)(vb[h] ? j0 + j : 0) * J.bcs;
-    }
     c64 ra[2][4], rb[4][4];
 
+    // Staging units: 4 consecutive kk of one row.  A: 512 units (128 rows x 4), B: 1024
+    // (256 rows x 4); thread tid owns A units tid + 256 h (h < 2) and B units tid + 256 h
+    // (h < 4), mapped so that a warp's global loads are contiguous along the operand's
+    // unit-stride dimension.  Conjugation is applied here; padding past kend, m or the
+    // tile width is zero.
     auto load = [&](int l0) {
-        const bool full = l0 + TC_BK <= kend;          // uniform over the CTA
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (va[h]) {
+            const int u = tid + 256 * h;
+            const int i = a_kfast ? (u >> 2) : (u & 127), q = a_kfast ? (u & 3) : (u >> 7);
+            const bool rok = i0 + i < J.m;
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    ra[h][e] = (full || l0 + 4 * qa[h] + e < kend) ? pa[h][e * acs] : mk<float>(0, 0);
+            for (int e = 0; e < 4; ++e) {
+                const int l = l0 + 4 * q + e;
+                c64 v = mk<float>(0, 0);
+                if (rok && l < kend) v = A[(int64_t)(i0 + i) * J.ars + (int64_t)l * J.acs];
+                ra[h][e] = conjA ? conj(v) : v;
             }
-            pa[h] += TC_BK * acs;
         }
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-            if (vb[h]) {
+            const int u = tid + 256 * h;
+            const int j = b_kfast ? (u >> 2) : (u & 255), q = b_kfast ? (u & 3) : (u >> 8);
+            const bool cok = j < w && j0 + j < J.n;
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    rb[h][e] = (full || l0 + 4 * qb[h] + e < kend) ? pb[h][e * brs] : mk<float>(0, 0);
+            for (int e = 0; e < 4; ++e) {
+                const int l = l0 + 4 * q + e;
+                c64 v = mk<float>(0, 0);
+                if (cok && l < kend) v = B[(int64_t)l * J.brs + (int64_t)(j0 + j) * J.bcs];
+                rb[h][e] = conjB ? conj(v) : v;
             }
-            pb[h] += TC_BK * brs;
         }
     };
     auto store = [&](int buf) {
         unsigned char *sa = smem + buf * TC_STAGE;
         unsigned char *sb = sa + 4 * TC_PLANE_A;
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-            if (va[h]) put4(sa, TC_PLANE_A, oa[h], ra[h]);
+        for (int h = 0; h < 2; ++h) {
+            const int u = tid + 256 * h;
+            const int i = a_kfast ? (u >> 2) : (u & 127), q = a_kfast ? (u & 3) : (u >> 7);
+            put4(sa, TC_PLANE_A, core_off(i, q), ra[h]);
+        }
 #pragma unroll
-        for (int h = 0; h < 4; ++h)
-            if (vb[h]) put4(sb, TC_PLANE_B, ob[h], rb[h]);
+        for (int h = 0; h < 4; ++h) {
+            const int u = tid + 256 * h;
+            const int j = b_kfast ? (u >> 2) : (u & 255), q = b_kfast ? (u & 3) : (u >> 8);
+            if (j < w) put4(sb, TC_PLANE_B, core_off(j, q), rb[h]);
+        }
     };
 
-    // Signs of the four real products (the planes hold A and B as stored; conjugation is
-    // a sign flip of Ai or Bi, taken by the negate-A bit of the instruction descriptor):
-    //   Cr = Ar Br - (sA Ai)(sB Bi),   Ci = Ar (sB Bi) + (sA Ai) Br,   sX = -1 if op(X) = conj(X)
-    const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
-    const uint32_t id_rr = instr_desc(w, false);
-    const uint32_t id_ii = instr_desc(w, conjA == conjB);      // - sA sB < 0 unless exactly one conj
-    const uint32_t id_ri = instr_desc(w, conjB);
-    const uint32_t id_ir = instr_desc(w, conjA);
+    // Cr = Ar Br - Ai Bi, Ci = Ar Bi + Ai Br on the (already conjugated) planes
+    const uint32_t id_rr = instr_desc(w, false), id_ii = instr_desc(w, true);
+    const uint32_t id_ri = id_rr, id_ir = id_rr;
     const uint32_t t_re = tmem, t_im = tmem + 256;
     bool ok = true;
     // Register staging runs two stages ahead of the MMAs: at step s the loads of stage s + 2
@@ -318,13 +303,13 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
                 mma_tf32(t_re, a0, b0, id_rr, first);       // Ar Br
                 mma_tf32(t_re, a0, b1, id_rr, 1u);
                 mma_tf32(t_re, a1, b0, id_rr, 1u);
-                mma_tf32(t_re, a2, b2, id_ii, 1u);          // -(sA Ai)(sB Bi)
+                mma_tf32(t_re, a2, b2, id_ii, 1u);          // - Ai Bi
                 mma_tf32(t_re, a2, b3, id_ii, 1u);
                 mma_tf32(t_re, a3, b2, id_ii, 1u);
-                mma_tf32(t_im, a0, b2, id_ri, first);       // Ar (sB Bi)
+                mma_tf32(t_im, a0, b2, id_ri, first);       // Ar Bi
                 mma_tf32(t_im, a0, b3, id_ri, 1u);
                 mma_tf32(t_im, a1, b2, id_ri, 1u);
-                mma_tf32(t_im, a2, b0, id_ir, 1u);          // (sA Ai) Br
+                mma_tf32(t_im, a2, b0, id_ir, 1u);          // Ai Br
                 mma_tf32(t_im, a2, b1, id_ir, 1u);
                 mma_tf32(t_im, a3, b0, id_ir, 1u);
             }

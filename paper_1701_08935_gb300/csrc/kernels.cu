@@ -67,7 +67,8 @@ __device__ __forceinline__ int find_job(const int32_t *tmap, const GJob *jobs, i
     return lo;
 }
 
-// C (=|-=) op(A) op(B) for every job in the list; one CTA per BM x BN tile.
+// C (=|-=) op(A) op(B) for every job in the list; one CTA per BM x BN tile (64 x 64, or
+// 32 x 128 for fronts with few pivot rows).
 // The whole kk extent of a tile is read before its C block is written, so a job
 // whose C aliases A (with n <= BN) or B (with m <= BM) is computed in place.
 template <class T, int BM, int BN, int BK>
@@ -94,7 +95,9 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
     const cx<T> *__restrict__ A = g.A[z] + J.a;
     const cx<T> *__restrict__ B = g.B[z] + J.b;
     const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
-    const int tx = tid & 15, ty = tid >> 4;
+    constexpr int TX = BN / 4, TY = BM / 4;             // 256 threads, 4 x 4 outputs each
+    static_assert(TX * TY == 256, "tile must give 256 threads");
+    const int tx = tid % TX, ty = tid / TX;
     cx<T> acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -126,9 +129,9 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
         for (int l = 0; l < BK; ++l) {
             cx<T> a[4], b[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[l][ty + 16 * r];
+            for (int r = 0; r < 4; ++r) a[r] = As[l][ty + TY * r];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Bs[l][tx + 16 * c];
+            for (int c = 0; c < 4; ++c) b[c] = Bs[l][tx + TX * c];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -140,11 +143,11 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
     const bool sub = J.flags & GJ_SUB, add = J.flags & GJ_ACC, atom = J.ks > 1;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const int i = i0 + ty + 16 * r;
+        const int i = i0 + ty + TY * r;
         if (i >= J.m) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const int j = j0 + tx + 16 * c;
+            const int j = j0 + tx + TX * c;
             if (j >= J.n) continue;
             cx<T> *p = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
             const cx<T> v = sub ? mk<T>(-acc[r][c].re, -acc[r][c].im) : acc[r][c];
@@ -301,6 +304,8 @@ void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops)
             launch_gemm_tc(g, grid, st);
         else if (g.bm == G2_BM)
             k_gemm_c64<<<grid, 256, 0, st>>>(g);
+        else if (g.bm == 32)
+            k_gemm<T, 32, 128, 16><<<grid, 256, 0, st>>>(g);
         else
             k_gemm<T, 64, 64, 16><<<grid, 256, 0, st>>>(g);
     } else {

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <numeric>
 #include "factor.h"
+#include "df64.cuh"
 
 namespace zolo {
 
@@ -42,13 +43,16 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
     return __uint_as_float(mag | (hi & 0x80000000u));
 }
 
-// part[b][t][c] = sum over this CTA's rows of conj(V_{j0+t}[i,c]) W[i,c], in FP32.
-// The projection coefficients of classical Gram-Schmidt only need FP32 accuracy: the
-// update W -= sum_j V_j h_j and the Hessenberg matrix use the same (rounded) h, so the
-// Arnoldi relation G V_m = V_{m+1} H_m stays exact to FP64 rounding and the basis is
-// orthonormal to ~1e-6, which keeps the least-squares residuals within 1e-4 of the
-// true ones.  The partial sums are reduced in FP64 by k_multidot_sum.
-__global__ void __launch_bounds__(256) k_multidot(int64_t n, int k, const c128 *const *__restrict__ V, int j0, int nj,
+// Krylov basis blocks are stored split: for V_j (n x k) the first n k float2 hold the
+// complex64 "hi" parts and the next n k the remainders, V = hi + lo to ~2^-47 (df_split).
+//
+// part[b][t][c] = sum over this CTA's rows of conj(V_{j0+t}[i,c]) W[i,c], in FP32 on the hi
+// parts.  The projection coefficients of classical Gram-Schmidt only need FP32 accuracy:
+// the update W -= sum_j V_j h_j and the Hessenberg matrix use the same h, so the Arnoldi
+// relation G V_m = V_{m+1} H_m stays exact to the update's rounding and the basis is
+// orthonormal to ~1e-6, which keeps the least-squares residuals within 1e-4 of the true
+// ones.  The partial sums are reduced in FP64 by k_multidot_sum.
+__global__ void __launch_bounds__(256) k_multidot(int64_t n, int k, const float2 *const *__restrict__ V, int j0, int nj,
                                                   const c128 *__restrict__ W, double2 *__restrict__ part) {
     for (int c = threadIdx.x; c < k; c += 256) {
         float ar[JT], ai[JT];
@@ -60,10 +64,9 @@ __global__ void __launch_bounds__(256) k_multidot(int64_t n, int k, const c128 *
 #pragma unroll
             for (int t = 0; t < JT; ++t)
                 if (t < nj) {
-                    const c128 v = V[j0 + t][i * k + c];
-                    const float vr = f64_to_f32_trunc(v.re), vi = f64_to_f32_trunc(v.im);
-                    ar[t] = fmaf(vr, wr, fmaf(vi, wi, ar[t]));        // conj(v) w
-                    ai[t] = fmaf(vr, wi, fmaf(-vi, wr, ai[t]));
+                    const float2 v = V[j0 + t][i * k + c];
+                    ar[t] = fmaf(v.x, wr, fmaf(v.y, wi, ar[t]));        // conj(v) w
+                    ai[t] = fmaf(v.x, wi, fmaf(-v.y, wr, ai[t]));
                 }
         }
 #pragma unroll
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(256) k_multidot(int64_t n, int k, const c128 *
 
 // h[j0 + t][c] (+)= sum_b part[b][t][c];  also H(j0+t, col, c) += that value
 __global__ void k_multidot_sum(int k, int nj, int parts, const double2 *__restrict__ part, c128 *__restrict__ h,
-                               int j0, c128 *__restrict__ H, int hld, int col) {
+                               float4 *__restrict__ hs, int j0, c128 *__restrict__ H, int hld, int col) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nj * k) return;
     const int t = idx / k, c = idx - t * k;
@@ -85,39 +88,66 @@ __global__ void k_multidot_sum(int k, int nj, int parts, const double2 *__restri
         s.im += v.y;
     }
     h[(int64_t)(j0 + t) * k + c] = s;
+    float4 sp;
+    df_split(s.re, sp.x, sp.y);
+    df_split(s.im, sp.z, sp.w);
+    hs[(int64_t)(j0 + t) * k + c] = sp;
     c128 *e = H + ((int64_t)c * hld + col) * hld + (j0 + t);     // H[c][col][row], column-major per c
     *e = *e + s;
 }
 
-// W[i,c] -= sum_{j < nj} V_j[i,c] h[j][c]
-__global__ void k_multiaxpy(int64_t n, int k, const c128 *const *__restrict__ V, int nj, const c128 *__restrict__ h,
+// W[i,c] -= sum_{j < nj} V_j[i,c] h[j][c]: the sum in double-float arithmetic on the FP32
+// pipe (split basis and split h), one FP64 subtraction per element at the end.
+__global__ void k_multiaxpy(int64_t n, int k, const float2 *const *__restrict__ V, int nj, const float4 *__restrict__ hs,
                             c128 *__restrict__ W) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * k) return;
+    const int64_t nk = n * k;
+    if (idx >= nk) return;
     const int c = (int)(idx % k);
-    c128 w = W[idx];
+    float srh = 0.f, srl = 0.f, sih = 0.f, sil = 0.f;
     for (int j = 0; j < nj; ++j) {
-        const c128 hv = h[(int64_t)j * k + c];
-        const c128 v = V[j][idx];
-        w.re -= v.re * hv.re - v.im * hv.im;
-        w.im -= v.re * hv.im + v.im * hv.re;
+        const float4 hv = hs[(int64_t)j * k + c];
+        const float2 vh = V[j][idx], vl = V[j][nk + idx];
+        df_fma(srh, srl, vh.x, vl.x, hv.x, hv.y);            // vr hr
+        df_fma(srh, srl, -vh.y, -vl.y, hv.z, hv.w);          // - vi hi
+        df_fma(sih, sil, vh.x, vl.x, hv.z, hv.w);            // vr hi
+        df_fma(sih, sil, vh.y, vl.y, hv.x, hv.y);            // vi hr
     }
+    c128 w = W[idx];
+    w.re = (w.re - df_widen(srh)) - df_widen(srl);
+    w.im = (w.im - df_widen(sih)) - df_widen(sil);
     W[idx] = w;
 }
 
-// norms[c] (sum of squares) -> scale column c of W by 1/sqrt; H(col+1, col, c) = sqrt
-__global__ void k_normalize(int64_t n, int k, const double *__restrict__ nrm2, c128 *__restrict__ W, c128 *__restrict__ H,
-                            int hld, int col) {
+// V = W / ||W_c|| per column c (norms[c] = sum of squares), stored split into the hi / lo
+// planes of P; H(col+1, col, c) = ||W_c|| when H is given.
+__global__ void k_normalize(int64_t n, int k, const double *__restrict__ nrm2, const c128 *__restrict__ W,
+                            float2 *__restrict__ P, c128 *__restrict__ H, int hld, int col) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < (int64_t)k && H) {
         const double nv = sqrt(nrm2[idx]);
         H[((int64_t)idx * hld + col) * hld + col + 1] = mk<double>(nv, 0.0);
     }
-    if (idx >= n * k) return;
+    const int64_t nk = n * k;
+    if (idx >= nk) return;
     const int c = (int)(idx % k);
     const double nv = sqrt(nrm2[c]);
     const double s = nv > 1e-300 ? 1.0 / nv : 0.0;
-    W[idx] = s * W[idx];
+    const c128 v = s * W[idx];
+    float2 hi, lo;
+    df_split(v.re, hi.x, lo.x);
+    df_split(v.im, hi.y, lo.y);
+    P[idx] = hi;
+    P[nk + idx] = lo;
+}
+
+// V (FP64, n x k) = hi + lo of a split basis block
+__global__ void k_from_planes(int64_t n, int k, const float2 *__restrict__ P, c128 *__restrict__ V) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nk = n * k;
+    if (idx >= nk) return;
+    const float2 hi = P[idx], lo = P[nk + idx];
+    V[idx] = mk<double>(df_widen(hi.x) + df_widen(lo.x), df_widen(hi.y) + df_widen(lo.y));
 }
 
 // Incremental Givens least squares for every (column c, shift s): append column `col`
@@ -205,14 +235,19 @@ __global__ void k_zeta(int k, int ns, int m, int mmax, const c128 *__restrict__ 
     zeta[(int64_t)j * k + c] = s;
 }
 // Y[i,c] = X[i,c]/2 + sum_{j<m} V_j[i,c] zeta[j][c]
-__global__ void k_combine(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx, const c128 *const *__restrict__ V,
+__global__ void k_combine(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx, const float2 *const *__restrict__ V,
                           int m, const c128 *__restrict__ zeta, c128 *__restrict__ Y, int64_t ldy) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * k) return;
+    const int64_t nk = n * k;
+    if (idx >= nk) return;
     const int64_t i = idx / k;
     const int c = (int)(idx - i * k);
     c128 y = 0.5 * X[i * ldx + c];
-    for (int j = 0; j < m; ++j) fma_acc(y, V[j][idx], zeta[(int64_t)j * k + c]);
+    for (int j = 0; j < m; ++j) {
+        const float2 hi = V[j][idx], lo = V[j][nk + idx];
+        const c128 v = mk<double>(df_widen(hi.x) + df_widen(lo.x), df_widen(hi.y) + df_widen(lo.y));
+        fma_acc(y, v, zeta[(int64_t)j * k + c]);
+    }
     Y[i * ldy + c] = y;
 }
 
@@ -438,7 +473,8 @@ struct KrylovWork {
     std::vector<c128 *> vhost;
     Buf vptr;                          // device copy of the block pointers
     int64_t vblk = 0;                  // elements per block the blocks were sized for
-    Buf H, h, part, nrm, beta, shifts, omega, res, lsq, zall, zeta;
+    Buf H, h, hs, part, nrm, beta, shifts, omega, res, lsq, zall, zeta;
+    Buf wcur, vcur;                    // FP64 n x k blocks: the vector being orthogonalised, and V_i
     Buf gram_part, At, Bt, U, Vt, W, Ah, Z, Qt, rot, dvec, off, idx, scl, jobs;
     Buf Y, AY, BY, Q, R;
 };
@@ -497,8 +533,14 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
     if (!rc) rc = grow(h, w.lsq, lsq_bytes);
     if (!rc) rc = grow(h, w.zall, pairs * mmax * sizeof(c128));
     if (!rc) rc = grow(h, w.zeta, (size_t)mmax * k * sizeof(c128));
+    if (!rc) rc = grow(h, w.hs, (size_t)(mmax + 1) * k * sizeof(float4));
+    if (!rc) rc = grow(h, w.wcur, (size_t)blk * sizeof(c128));
+    if (!rc) rc = grow(h, w.vcur, (size_t)blk * sizeof(c128));
     if (rc) return rc;
-    const c128 *const *Vp = (const c128 *const *)w.vptr.p;
+    const float2 *const *Vp = (const float2 *const *)w.vptr.p;      // split basis blocks
+    c128 *Wc = (c128 *)w.wcur.p, *Vc = (c128 *)w.vcur.p;
+    float4 *hsp = (float4 *)w.hs.p;
+    auto plane = [&](int j) { return (float2 *)w.vhost[j]; };
     c128 *H = (c128 *)w.H.p;
     c128 *hv = (c128 *)w.h.p;
     double *nrm = (double *)w.nrm.p, *beta = (double *)w.beta.p, *res = (double *)w.res.p;
@@ -529,11 +571,11 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
     {
         LinArgs a;
         std::memset(&a, 0, sizeof(a));
-        a.n = n; a.k = k; a.ldy = k; a.Y = w.vhost[0]; a.nterm = 1;
+        a.n = n; a.k = k; a.ldy = k; a.Y = Wc; a.nterm = 1;
         a.coef[0] = c128{1.0, 0.0}; a.X[0] = X; a.ldx[0] = ldx;
         launch_lincomb(a, st);
-        launch_colnorm2(n, k, w.vhost[0], k, nrm, st);
-        k_normalize<<<nblk(blk), 256, 0, st>>>(n, (int)k, nrm, w.vhost[0], nullptr, hld, 0);
+        launch_colnorm2(n, k, Wc, k, nrm, st);
+        k_normalize<<<nblk(blk), 256, 0, st>>>(n, (int)k, nrm, Wc, plane(0), nullptr, hld, 0);
         count_launch();
         // beta = sqrt(nrm): reuse the normalise kernel's formula on a k-vector
     }
@@ -567,12 +609,14 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
     for (int i = 0; i < mmax; ++i) {
         rc = ensure_block(i + 1);
         if (rc) return rc;
-        c128 *Wv = w.vhost[i + 1];
+        c128 *Wv = Wc;
         if (h->prec == ZOLO_PREC_MIXED) {
             const double prev = (i == 0) ? 1.0 : std::max(worst, 1e-300);
             h->refine_tol_now = std::min(1e-3, std::max(rtol, 1e-2 * tol / prev));
         }
-        rc = apply_inner(h, k, w.vhost[i], k, Wv, k, st);
+        k_from_planes<<<nblk(blk), 256, 0, st>>>(n, (int)k, plane(i), Vc);
+        count_launch();
+        rc = apply_inner(h, k, Vc, k, Wv, k, st);
         if (rc) {                                          // a failed inner solve is not a short GMRES
             h->inner_failed = true;
             return rc;
@@ -586,10 +630,10 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
                 k_multidot<<<RED_CTAS, 256, 0, st>>>(n, (int)k, Vp, j0, nj, Wv, (double2 *)w.part.p);
                 count_launch();
                 k_multidot_sum<<<nblk((int64_t)nj * k), 256, 0, st>>>((int)k, nj, RED_CTAS, (const double2 *)w.part.p,
-                                                                     hv, j0, H, hld, i);
+                                                                     hv, hsp, j0, H, hld, i);
                 count_launch();
             }
-            k_multiaxpy<<<nblk(blk), 256, 0, st>>>(n, (int)k, Vp, i + 1, hv, Wv);
+            k_multiaxpy<<<nblk(blk), 256, 0, st>>>(n, (int)k, Vp, i + 1, hsp, Wv);
             count_launch();
             if (pass == 0) {
                 launch_colnorm2(n, k, Wv, k, nrm, st);
@@ -603,7 +647,7 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
             }
         }
         launch_colnorm2(n, k, Wv, k, nrm, st);
-        k_normalize<<<nblk(blk), 256, 0, st>>>(n, (int)k, nrm, Wv, H, hld, i);
+        k_normalize<<<nblk(blk), 256, 0, st>>>(n, (int)k, nrm, Wv, plane(i + 1), H, hld, i);
         count_launch();
         k_lsq_step<<<nblk((int64_t)pairs, 128), 128, 0, st>>>((int)k, ns, (const c128 *)w.shifts.p, H, hld, i, beta, S, mmax,
                                                          res);

@@ -93,8 +93,8 @@ extern "C" int zolo_solve_noalloc(zolo_factor_h h, int32_t pole, int32_t herm, i
                 g.tmap[0] = L.tmoff >= 0 ? h->d_stmap + L.tmoff : nullptr;
                 g.njobs[0] = L.cnt;
                 g.ntiles[0] = L.ntiles;
-                g.A[0] = basep(L.swap_ab ? o.bbase : o.abase);
-                g.B[0] = basep(L.swap_ab ? o.abase : o.bbase);
+                g.A[0] = basep(o.abase);
+                g.B[0] = basep(o.bbase);
                 g.C[0] = basep(o.cbase);
                 launch_gemm<double>(g, 1, st, L.flops);
             } else {
