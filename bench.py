@@ -345,6 +345,9 @@ def run_ours(args):
                  "n_gmres": stats["n_gmres"], "n_refine_max": stats["n_refine_max"], "max_resid": stats["max_resid"],
                  "relerr": stats["relerr"], "t_factor_ms": stats["t_factor_ms"], "t_apply_ms": stats["t_apply_ms"],
                  "t_rr_ms": stats["t_rr_ms"], "solve_cols": stats["solve_cols"]},
+        "filter_apply_ms": stats["t_apply_ms"] / max(1, stats["n_iter"]),
+        "filter_apply_note": "mean device time of one filter application (Algorithm 2 on the k-column block, "
+                             "all GMRES chunks) inside the timed step",
         "gpu_launches": int(prof["launches"]),
         "roofline": roof,
         "clocks": clk,

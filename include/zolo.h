@@ -266,6 +266,22 @@ int  zolo_eigs(const zolo_csr *A, const zolo_csr *B, double a, double b, int64_t
                int64_t ldv, int64_t cap, int64_t *n_found, double *resid, zolo_stats *stats,
                void *stream);
 
+/* Spectrum slicing (Section 3.2: eigenpairs in different spectrum ranges are independent
+ * problems).  Every eigenpair with bounds[s] < lambda < bounds[s+1] for some s < nslice;
+ * bounds strictly increasing.  One symbolic analysis is shared; per slice the count comes
+ * from Sylvester inertia at its bounds (zolo_inertia), the filter from the slice and
+ * opts->gap_rel (gaps of gap_rel times the slice width on both sides), r1 / r2 / k from opts
+ * (k <= 0: ceil(1.5 count) + 8), then a factorisation and Algorithm 1.  Results are
+ * concatenated slice by slice (ascending): evals[cap], evecs (device, n x cap, row-major,
+ * ld = ldv, B-orthonormal within a slice), resid[cap] (may be NULL), slice_of[cap] (slice
+ * index of each pair, may be NULL).  EINVAL with *n_found = the total count when cap is
+ * too small.  ENOCONV when a slice did not converge or found fewer pairs than its count;
+ * the pairs found are still returned.  stats: sums of times and solves, maxima of counts
+ * and residuals over the slices.                                                   */
+int  zolo_eigs_slices(const zolo_csr *A, const zolo_csr *B, int32_t nslice, const double *bounds,
+                      const zolo_opts *opts, double *evals, void *evecs, int64_t ldv, int64_t cap,
+                      int64_t *n_found, double *resid, int32_t *slice_of, zolo_stats *stats, void *stream);
+
 /* ---- measurement hooks (no counterpart in the paper) ---------------------- */
 /* Count the library's kernel launches from now on; gemm_events selects which dense-
  * product (GEMM) launches are bracketed with CUDA events: bit 0 complex64, bit 1

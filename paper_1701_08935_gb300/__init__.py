@@ -116,13 +116,15 @@ _sig("zolo_eigs_factored", C.c_int, [_vp, _dbl, _dbl, _i64, _vp, _vp, _vp, _i64,
                                      _P(Stats), _vp])
 _sig("zolo_eigs", C.c_int, [_P(Csr), _P(Csr), _dbl, _dbl, _i64, _P(FilterSpec), _P(Opts), _vp, _vp, _i64,
                             _i64, _P(_i64), _vp, _P(Stats), _vp])
+_sig("zolo_eigs_slices", C.c_int, [_P(Csr), _P(Csr), C.c_int32, _vp, _P(Opts), _vp, _vp, _i64, _i64, _P(_i64), _vp,
+                                   _vp, _P(Stats), _vp])
 
 EXPORTED = ["zolo_opts_default", "zolo_strerror", "zolo_last_error", "zolo_version", "zolo_filter_build",
             "zolo_filter_get_info", "zolo_filter_eval", "zolo_filter_destroy", "zolo_analyze",
             "zolo_symbolic_get_info", "zolo_symbolic_export", "zolo_symbolic_destroy", "zolo_factor",
             "zolo_refactor", "zolo_inertia", "zolo_solve_noalloc", "zolo_profile_begin", "zolo_profile_end",
             "zolo_profile_tc", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
-            "zolo_apply_inner", "zolo_apply", "zolo_eigs_factored", "zolo_eigs"]
+            "zolo_apply_inner", "zolo_apply", "zolo_eigs_factored", "zolo_eigs", "zolo_eigs_slices"]
 
 
 def _check(st, where):
@@ -233,6 +235,31 @@ def inertia(A, B, shifts, sym=None, opts=None, stream=None):
     _check(lib.zolo_inertia(C.byref(hA.s), C.byref(hB.s), sym.h if sym is not None else None, C.byref(o),
                             len(sh), sh.ctypes.data, out.ctypes.data, _stream(stream)), "zolo_inertia")
     return out
+
+
+def eigs_slices(A, B, bounds, opts=None, cap=None, stream=None):
+    """Eigenpairs in every slice (bounds[s], bounds[s+1]) (zolo_eigs_slices): returns
+    (evals, V (device, n x found), resid, slice_of, stats, status)."""
+    import torch
+    hA, hB = HostCsr(A), HostCsr(B)
+    bd = np.ascontiguousarray(np.asarray(bounds, dtype=np.float64))
+    o = opts if opts is not None else default_opts()
+    n = A.shape[0]
+    if cap is None:
+        cnt = inertia(A, B, bd[[0, -1]], opts=o, stream=stream)
+        cap = int(cnt[1] - cnt[0])
+    evals, resid = np.zeros(max(cap, 1)), np.zeros(max(cap, 1))
+    sl = np.zeros(max(cap, 1), dtype=np.int32)
+    V = torch.zeros((n, max(cap, 1)), dtype=torch.complex128, device="cuda")
+    nf = _i64(0)
+    st = Stats()
+    rc = lib.zolo_eigs_slices(C.byref(hA.s), C.byref(hB.s), len(bd) - 1, bd.ctypes.data, C.byref(o),
+                              evals.ctypes.data, _vp(V.data_ptr()), max(cap, 1), cap, C.byref(nf),
+                              resid.ctypes.data, sl.ctypes.data, C.byref(st), _stream(stream))
+    if rc not in (OK, ENOCONV):
+        _check(rc, "zolo_eigs_slices")
+    m = int(nf.value)
+    return evals[:m], V[:, :m], resid[:m], sl[:m], st.as_dict(), rc
 
 
 def profile_begin(gemm_events=0):

@@ -21,9 +21,9 @@
 // tensor memory: Cr in columns [0, 256), Ci in [256, 512) of a 512-column allocation.
 // Operands are staged by all 256 threads (global loads, conjugation, hi/lo split, stores
 // in the canonical no-swizzle K-major layout) into one of two 96 KB shared-memory stages
-// while the MMAs of the other stage run, with the global loads of the stage after that
-// already in flight; one elected thread issues the MMAs and commits them to the stage's
-// mbarrier.  Every wait on an mbarrier is bounded in time (2 s): on
+// while the MMAs of the other stage run, with the global loads of the next two stages
+// already in flight (two register sets); one elected thread issues the MMAs and commits
+// them to the stage's mbarrier.  Every wait on an mbarrier is bounded in time (2 s): on
 // expiry the CTA skips its remaining waits and its epilogue, records ZOLO_ETIMEOUT in a
 // device status word (read by gemm_tc_status) and releases its tensor memory.
 #include "kernels.cuh"
@@ -223,14 +223,14 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
     const c64 *__restrict__ B = g.B[z] + J.b;
     const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
     const bool a_kfast = (J.acs == 1), b_kfast = (J.brs == 1);
-    c64 ra[2][4], rb[4][4];
+    c64 ra0[2][4], rb0[4][4], ra1[2][4], rb1[4][4];         // two register stages
 
     // Staging units: 4 consecutive kk of one row.  A: 512 units (128 rows x 4), B: 1024
     // (256 rows x 4); thread tid owns A units tid + 256 h (h < 2) and B units tid + 256 h
     // (h < 4), mapped so that a warp's global loads are contiguous along the operand's
     // unit-stride dimension.  Conjugation is applied here; padding past kend, m or the
     // tile width is zero.
-    auto load = [&](int l0) {
+    auto load = [&](int l0, c64 (&ra)[2][4], c64 (&rb)[4][4]) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int u = tid + 256 * h;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
             }
         }
     };
-    auto store = [&](int buf) {
+    auto store = [&](int buf, const c64 (&ra)[2][4], const c64 (&rb)[4][4]) {
         unsigned char *sa = smem + buf * TC_STAGE;
         unsigned char *sb = sa + 4 * TC_PLANE_A;
 #pragma unroll
@@ -280,12 +280,11 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
     const uint32_t id_ri = id_rr, id_ir = id_rr;
     const uint32_t t_re = tmem, t_im = tmem + 256;
     bool ok = true;
-    // Register staging runs two stages ahead of the MMAs: at step s the loads of stage s + 2
-    // are issued right after stage s + 1 is stored, so they have a whole stage of MMAs to land.
-    load(kbeg);
-    store(0);
-    if (nst > 1) load(kbeg + TC_BK);
-    for (int s = 0; s < nst; ++s) {
+    // One pipeline step: the MMAs of stage s from shared buffer s % 2, then (once the MMAs of
+    // stage s - 1 have released the other buffer) stage s + 1 is stored from the register
+    // set (ra, rb) and that set is refilled with the loads of stage s + 3.  Two register sets
+    // alternate, so every global load has two steps to land before it is stored.
+    auto step = [&](int s, c64 (&ra)[2][4], c64 (&rb)[4][4]) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -316,11 +315,18 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
             mma_commit(mb0 + 8 * (s & 1));
         }
         if (s + 1 < nst) {
-            // the other buffer is free once the MMAs of stage s - 1 are done
             if (ok && s >= 1 && !mbar_wait(mb0 + 8 * ((s - 1) & 1), ((s - 1) >> 1) & 1)) ok = false;
-            store((s + 1) & 1);
-            if (s + 2 < nst) load(kbeg + TC_BK * (s + 2));
+            store((s + 1) & 1, ra, rb);
+            if (s + 3 < nst) load(kbeg + TC_BK * (s + 3), ra, rb);
         }
+    };
+    load(kbeg, ra0, rb0);
+    store(0, ra0, rb0);
+    if (nst > 1) load(kbeg + TC_BK, ra1, rb1);          // stage 1 -> set 1
+    if (nst > 2) load(kbeg + 2 * TC_BK, ra0, rb0);      // stage 2 -> set 0
+    for (int s = 0; s < nst; s += 2) {
+        step(s, ra1, rb1);                              // stores stage s + 1 (odd) from set 1
+        if (s + 1 < nst) step(s + 1, ra0, rb0);         // stores stage s + 2 (even) from set 0
     }
     if (ok && !mbar_wait(mb0 + 8 * ((nst - 1) & 1), ((nst - 1) >> 1) & 1)) ok = false;
     fence_after_sync();

@@ -71,8 +71,10 @@ __device__ __forceinline__ int find_job(const int32_t *tmap, const GJob *jobs, i
 // 32 x 128 for fronts with few pivot rows).
 // The whole kk extent of a tile is read before its C block is written, so a job
 // whose C aliases A (with n <= BN) or B (with m <= BM) is computed in place.
+// complex64: three CTAs per SM (<= 85 registers): tiles of the deep tree levels are short
+// in kk, so their global-memory latency is hidden by resident CTAs rather than the k-loop.
 template <class T, int BM, int BN, int BK>
-__global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T> g) {
     const int z = blockIdx.z;
     const int tile = blockIdx.x;
     if (tile >= g.ntiles[z]) return;

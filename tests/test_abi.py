@@ -74,3 +74,17 @@ def test_bad_tensor_core_policy_rejected_before_any_device_work():
             Z.Factor(p.A, p.B, f, opts=Z.default_opts(grid=(6, 6), precision=Z.PREC_MIXED, tensor_core=bad),
                      stream=0)
         assert e.value.status == Z.EINVAL
+
+
+def test_slices_reject_bad_bounds_before_any_device_work():
+    import ctypes as C
+    p = synth.pencil_2d_real(6, seed=1)
+    hA, hB = Z.HostCsr(p.A), Z.HostCsr(p.B)
+    o = Z.default_opts(grid=(6, 6))
+    for bounds in ([0.5, 0.5, 1.0], [0.0, float("nan"), 1.0], [1.0, 0.5]):
+        bd = np.asarray(bounds, dtype=np.float64)
+        ev = np.zeros(4)
+        nf = C.c_int64(0)
+        rc = Z.lib.zolo_eigs_slices(C.byref(hA.s), C.byref(hB.s), len(bd) - 1, bd.ctypes.data, C.byref(o),
+                                    ev.ctypes.data, C.c_void_p(1), 4, 4, C.byref(nf), None, None, None, None)
+        assert rc == Z.EINVAL
