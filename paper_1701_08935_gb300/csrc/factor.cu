@@ -94,11 +94,11 @@ constexpr double TC_MIN_ROWS = 128.0;
 
 // Append a launch of GEMM jobs (empty products dropped) and return its descriptor.
 // Complex64 launches whose jobs average >= TC_MIN_ROWS rows run on the tensor-core kernel
-// (128 x <= 256 tiles; every complex64 launch with ZOLO_TC_ALWAYS, none with ZOLO_TC_OFF,
-// where they take 128 x 64 FP32 tiles instead); other launches take 64 x 64 tiles.
-// With allow_split, a launch with fewer than ~4 waves of tiles (2 for the tensor-core
-// kernel, one CTA per SM) splits the kk extent of its accumulating jobs (GJ_SUB / GJ_ACC,
-// kk >= 512) over several CTAs (atomic adds).
+// (128 x <= 128 tiles; every complex64 launch with ZOLO_TC_ALWAYS, none with ZOLO_TC_OFF,
+// where they take 128 x 64 FP32 tiles instead); other launches take 64 x 64 tiles (32 x 128
+// when the jobs average <= 40 rows).  With allow_split, a launch with fewer than ~4 waves
+// of tiles splits the kk extent of its accumulating jobs (GJ_SUB / GJ_ACC, kk >= 512) over
+// several CTAs (atomic adds).
 Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool allow_split = false) {
     Launch L;
     L.off = (int64_t)all.size();
@@ -119,7 +119,8 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
     if (g_plan_c64 && cnt &&
         (g_plan_tc == ZOLO_TC_ALWAYS || (g_plan_tc == ZOLO_TC_AUTO && msum / cnt >= TC_MIN_ROWS))) {
         L.bm = 128;
-        L.bn = 256;
+        L.bn = 128;
+        L.tc = true;
     }
     auto splittable = [](const GJob &j) { return (j.flags & (GJ_SUB | GJ_ACC)) && j.k >= 512; };
     auto split_of = [&](const GJob &j, int f) { return splittable(j) ? std::max(1, std::min({f, j.k / 256, 16})) : 1; };
@@ -128,9 +129,9 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
     for (const GJob &j : jobs)
         if (j.m > 0 && j.n > 0 && j.k > 0) base += tiles_of(j);
     int factor = 1;
-    if (allow_split && base > 0 && L.bn == 256 && base < 4 * 152) {
-        // one CTA per SM: model the launch as waves x (k-stages of the longest slice + ~4
-        // stages of prologue and epilogue) and take the split that minimises it
+    if (allow_split && base > 0 && L.tc && base < 8 * 152) {
+        // two CTAs per SM: model the launch as waves x (k-stages of 8 of the longest slice +
+        // ~8 stages of prologue and epilogue) and take the split that minimises it
         double best = 1e300;
         for (int f = 1; f <= 16; ++f) {
             int64_t t = 0;
@@ -139,9 +140,9 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
                 if (j.m > 0 && j.n > 0 && j.k > 0) {
                     const int ks = split_of(j, f);
                     t += (int64_t)tiles_of(j) * ks;
-                    stages = std::max(stages, ((j.k + ks - 1) / ks + 15) / 16);
+                    stages = std::max(stages, ((j.k + ks - 1) / ks + 7) / 8);
                 }
-            const double cost = std::ceil((double)t / 152.0) * (stages + 4);
+            const double cost = std::ceil((double)t / 304.0) * (stages + 8);
             if (cost < best * (1.0 - 1e-9)) {
                 best = cost;
                 factor = f;

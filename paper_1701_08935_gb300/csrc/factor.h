@@ -13,7 +13,8 @@ struct Launch {
     int ntiles = 0;      // CTAs
     double flops = 0.0;  // executed flops of a GEMM launch (8 m n k summed over jobs)
     int bm = 64;         // GEMM tile height of the launch
-    int bn = 64;         // GEMM tile width (256: complex64 tensor-core kernel)
+    int bn = 64;         // GEMM tile width
+    bool tc = false;     // complex64 tensor-core kernel (bm = bn = 128)
     int64_t tmoff = -1;  // first entry of the launch's tile -> job map (-1: none)
 };
 

@@ -16,16 +16,18 @@
 // accurate as the FP32 SIMT kernels up to a small factor; the FP64 refinement of every
 // mixed-precision solve absorbs the difference.
 //
-// Tiles: one CTA per 128 x w tile of C, w <= 256 columns chosen per job so that the
-// ceil(n / 256) column tiles have equal width (a multiple of 16).  Accumulators live in
-// tensor memory: Cr in columns [0, 256), Ci in [256, 512) of a 512-column allocation.
-// Operands are staged by all 256 threads (global loads, conjugation, hi/lo split, stores
-// in the canonical no-swizzle K-major layout) into one of two 96 KB shared-memory stages
-// while the MMAs of the other stage run, with the global loads of the next two stages
-// already in flight (two register sets); one elected thread issues the MMAs and commits
-// them to the stage's mbarrier.  Every wait on an mbarrier is bounded in time (2 s): on
-// expiry the CTA skips its remaining waits and its epilogue, records ZOLO_ETIMEOUT in a
-// device status word (read by gemm_tc_status) and releases its tensor memory.
+// Tiles: one CTA per 128 x w tile of C, w <= 128 columns chosen per job so that the
+// ceil(n / 128) column tiles have equal width (a multiple of 16).  Two CTAs share an SM, so
+// the global-memory latencies of one (job lookup, first stages, epilogue) overlap the MMAs of
+// the other: each allocates 256 tensor-memory columns (Cr in [0, 128), Ci in [128, 256)) and
+// 96 KB of shared memory, three stages of k = 8.  All 256 threads stage the operands (global
+// loads, conjugation, hi/lo split, 16-byte stores in the canonical no-swizzle K-major layout,
+// each quarter-warp writing 128 contiguous bytes); one elected thread issues the MMAs of a
+// stage and commits them to the stage's mbarrier, and a buffer is refilled once the MMAs of
+// the stage that used it have completed, two stages later.  Every wait on an mbarrier is
+// bounded in time (2 s): on expiry the CTA skips its remaining waits and its epilogue,
+// records ZOLO_ETIMEOUT in a device status word (read by gemm_tc_status) and releases its
+// tensor memory.
 #include "kernels.cuh"
 #include "zolo.h"
 
@@ -36,29 +38,30 @@ namespace zolo {
 namespace {
 
 constexpr int TC_BM = 128;                 // rows of a C tile (MMA M)
-constexpr int TC_BN = 256;                 // widest C tile (MMA N)
-constexpr int TC_BK = 16;                  // complex k-extent of a stage (two MMA k-steps of 8)
-constexpr int TC_PLANE_A = TC_BM * TC_BK * 4;        // bytes of one A plane (8 KB)
-constexpr int TC_PLANE_B = TC_BN * TC_BK * 4;        // bytes of one B plane (16 KB)
-constexpr int TC_STAGE = 4 * TC_PLANE_A + 4 * TC_PLANE_B;   // 96 KB
-constexpr int TC_SMEM = 2 * TC_STAGE + 64;                  // + mbarriers, TMEM slot, job index
-constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr int TC_BN = 128;                 // widest C tile (MMA N)
+constexpr int TC_BK = 8;                   // complex k-extent of a stage (one MMA k-step)
+constexpr int TC_NSTAGE = 3;               // shared-memory stages
+constexpr int TC_PLANE_A = TC_BM * TC_BK * 4;        // bytes of one A plane (4 KB)
+constexpr int TC_PLANE_B = TC_BN * TC_BK * 4;        // bytes of one B plane (4 KB)
+constexpr int TC_STAGE = 4 * TC_PLANE_A + 4 * TC_PLANE_B;   // 32 KB
+constexpr int TC_SMEM = TC_NSTAGE * TC_STAGE + 64;          // + mbarriers, TMEM slot, job index
+constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;              // 2 s per mbarrier wait at most
 
 __device__ int g_tc_status = 0;
 
-// Byte offset of element (row, kk) (kk < 16) inside a plane in the canonical no-swizzle
-// K-major layout: 8-row x 16-byte core matrices, stored contiguously (128 B each), the
-// four core matrices of a row group adjacent along K (LBO = 128 B) and row groups 512 B
-// apart (SBO).
+// Byte offset of the 4-element group q (kk = 4q .. 4q+3, q < 2) of row `row` inside a plane
+// in the canonical no-swizzle K-major layout: 8-row x 16-byte core matrices stored
+// contiguously (128 B each), the two core matrices of a row group adjacent along K
+// (LBO = 128 B) and row groups 256 B apart (SBO).
 __device__ __forceinline__ uint32_t core_off(int row, int q) {
-    return (uint32_t)(((row >> 3) * 4 + q) * 128 + (row & 7) * 16);
+    return (uint32_t)(((row >> 3) * 2 + q) * 128 + (row & 7) * 16);
 }
 
 // Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), version 1,
 // no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    const uint64_t lbo = 128 >> 4, sbo = 512 >> 4;
+    const uint64_t lbo = 128 >> 4, sbo = 256 >> 4;
     return (uint64_t)((addr & 0x3FFFF) >> 4) | (lbo << 16) | (sbo << 32) | (1ull << 46);
 }
 
@@ -154,14 +157,14 @@ __device__ __forceinline__ void put4(unsigned char *planes, int plane_bytes, uin
     *reinterpret_cast<float4 *>(planes + 3 * plane_bytes + off) = make_float4(il[0], il[1], il[2], il[3]);
 }
 
-__global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
+__global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
     const int z = blockIdx.z;
     const int tile = blockIdx.x;
     if (tile >= g.ntiles[z]) return;
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGE);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * TC_STAGE + 16);
-    int *s_job = reinterpret_cast<int *>(smem + 2 * TC_STAGE + 20);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + TC_NSTAGE * TC_STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + TC_NSTAGE * TC_STAGE + 8 * TC_NSTAGE);
+    int *s_job = reinterpret_cast<int *>(smem + TC_NSTAGE * TC_STAGE + 8 * TC_NSTAGE + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GJob *jobs = g.jobs[z];
     if (tid == 0) {
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
     const GJob J = jobs[*s_job];
     int t = tile - J.tile0;
     const int ntn = (J.n + TC_BN - 1) / TC_BN;
-    const int w = ((J.n + ntn - 1) / ntn + 15) / 16 * 16;     // tile width, <= 256
+    const int w = ((J.n + ntn - 1) / ntn + 15) / 16 * 16;     // tile width, <= 128
     const int tmn = J.tm * ntn;
     const int kslice = t / tmn;
     t -= kslice * tmn;
@@ -210,8 +213,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8) : "memory");
+        for (int b = 0; b < TC_NSTAGE; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8 * b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before_sync();
@@ -222,113 +225,87 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(GemmArgs<float> g) {
     const c64 *__restrict__ A = g.A[z] + J.a;
     const c64 *__restrict__ B = g.B[z] + J.b;
     const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
-    const bool a_kfast = (J.acs == 1), b_kfast = (J.brs == 1);
-    c64 ra0[2][4], rb0[4][4], ra1[2][4], rb1[4][4];         // two register stages
-
-    // Staging units: 4 consecutive kk of one row.  A: 512 units (128 rows x 4), B: 1024
-    // (256 rows x 4); thread tid owns A units tid + 256 h (h < 2) and B units tid + 256 h
-    // (h < 4), mapped so that a warp's global loads are contiguous along the operand's
-    // unit-stride dimension.  Conjugation is applied here; padding past kend, m or the
-    // tile width is zero.
-    auto load = [&](int l0, c64 (&ra)[2][4], c64 (&rb)[4][4]) {
+    // Staging unit of a thread: 4 consecutive kk (q = 0 or 1) of one row of A and one row
+    // of B (as N x K).  Along a unit-stride row index, the warp's lanes take consecutive
+    // rows (coalesced loads); along a unit-stride kk, 8 lanes take 8 consecutive rows of one
+    // q.  Either way each quarter-warp stores 128 contiguous bytes per plane.
+    int ia, qa, jb, qb;
+    if (J.acs == 1) { ia = 8 * (tid >> 4) + (tid & 7); qa = (tid >> 3) & 1; }
+    else { ia = tid & 127; qa = tid >> 7; }
+    if (J.brs == 1) { jb = 8 * (tid >> 4) + (tid & 7); qb = (tid >> 3) & 1; }
+    else { jb = tid & 127; qb = tid >> 7; }
+    const bool va = i0 + ia < J.m, vb = jb < w && j0 + jb < J.n;
+    const uint32_t oa = core_off(ia, qa), ob = core_off(jb, qb);
+    c64 ra[4], rb[4];
+    auto load = [&](int l0) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int u = tid + 256 * h;
-            const int i = a_kfast ? (u >> 2) : (u & 127), q = a_kfast ? (u & 3) : (u >> 7);
-            const bool rok = i0 + i < J.m;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int l = l0 + 4 * q + e;
-                c64 v = mk<float>(0, 0);
-                if (rok && l < kend) v = A[(int64_t)(i0 + i) * J.ars + (int64_t)l * J.acs];
-                ra[h][e] = conjA ? conj(v) : v;
-            }
+        for (int e = 0; e < 4; ++e) {
+            const int l = l0 + 4 * qa + e;
+            c64 v = mk<float>(0, 0);
+            if (va && l < kend) v = A[(int64_t)(i0 + ia) * J.ars + (int64_t)l * J.acs];
+            ra[e] = conjA ? conj(v) : v;
         }
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int u = tid + 256 * h;
-            const int j = b_kfast ? (u >> 2) : (u & 255), q = b_kfast ? (u & 3) : (u >> 8);
-            const bool cok = j < w && j0 + j < J.n;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int l = l0 + 4 * q + e;
-                c64 v = mk<float>(0, 0);
-                if (cok && l < kend) v = B[(int64_t)l * J.brs + (int64_t)(j0 + j) * J.bcs];
-                rb[h][e] = conjB ? conj(v) : v;
-            }
+        for (int e = 0; e < 4; ++e) {
+            const int l = l0 + 4 * qb + e;
+            c64 v = mk<float>(0, 0);
+            if (vb && l < kend) v = B[(int64_t)l * J.brs + (int64_t)(j0 + jb) * J.bcs];
+            rb[e] = conjB ? conj(v) : v;
         }
     };
-    auto store = [&](int buf, const c64 (&ra)[2][4], const c64 (&rb)[4][4]) {
+    auto store = [&](int buf) {
         unsigned char *sa = smem + buf * TC_STAGE;
-        unsigned char *sb = sa + 4 * TC_PLANE_A;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int u = tid + 256 * h;
-            const int i = a_kfast ? (u >> 2) : (u & 127), q = a_kfast ? (u & 3) : (u >> 7);
-            put4(sa, TC_PLANE_A, core_off(i, q), ra[h]);
-        }
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int u = tid + 256 * h;
-            const int j = b_kfast ? (u >> 2) : (u & 255), q = b_kfast ? (u & 3) : (u >> 8);
-            if (j < w) put4(sb, TC_PLANE_B, core_off(j, q), rb[h]);
-        }
+        put4(sa, TC_PLANE_A, oa, ra);
+        if (jb < w) put4(sa + 4 * TC_PLANE_A, TC_PLANE_B, ob, rb);
     };
 
     // Cr = Ar Br - Ai Bi, Ci = Ar Bi + Ai Br on the (already conjugated) planes
-    const uint32_t id_rr = instr_desc(w, false), id_ii = instr_desc(w, true);
-    const uint32_t id_ri = id_rr, id_ir = id_rr;
-    const uint32_t t_re = tmem, t_im = tmem + 256;
+    const uint32_t id_pos = instr_desc(w, false), id_neg = instr_desc(w, true);
+    const uint32_t t_re = tmem, t_im = tmem + 128;
     bool ok = true;
-    // One pipeline step: the MMAs of stage s from shared buffer s % 2, then (once the MMAs of
-    // stage s - 1 have released the other buffer) stage s + 1 is stored from the register
-    // set (ra, rb) and that set is refilled with the loads of stage s + 3.  Two register sets
-    // alternate, so every global load has two steps to land before it is stored.
-    auto step = [&](int s, c64 (&ra)[2][4], c64 (&rb)[4][4]) {
+    // Step s: the MMAs of stage s (buffer s % 3); then, once the MMAs of stage s - 2 have
+    // released buffer (s + 1) % 3, stage s + 1 is stored from registers and the loads of
+    // stage s + 2 are issued.
+    load(kbeg);
+    store(0);
+    if (nst > 1) load(kbeg + TC_BK);
+    for (int s = 0; s < nst; ++s) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        const int buf = s % TC_NSTAGE;
         if (tid == 0) {
             fence_after_sync();
-            const uint32_t sa = sbase + (s & 1) * TC_STAGE, sb = sa + 4 * TC_PLANE_A;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t a0 = smem_desc(sa + ks * 256), a1 = smem_desc(sa + TC_PLANE_A + ks * 256),
-                               a2 = smem_desc(sa + 2 * TC_PLANE_A + ks * 256),
-                               a3 = smem_desc(sa + 3 * TC_PLANE_A + ks * 256);
-                const uint64_t b0 = smem_desc(sb + ks * 256), b1 = smem_desc(sb + TC_PLANE_B + ks * 256),
-                               b2 = smem_desc(sb + 2 * TC_PLANE_B + ks * 256),
-                               b3 = smem_desc(sb + 3 * TC_PLANE_B + ks * 256);
-                const uint32_t first = (s == 0 && ks == 0) ? 0u : 1u;
-                mma_tf32(t_re, a0, b0, id_rr, first);       // Ar Br
-                mma_tf32(t_re, a0, b1, id_rr, 1u);
-                mma_tf32(t_re, a1, b0, id_rr, 1u);
-                mma_tf32(t_re, a2, b2, id_ii, 1u);          // - Ai Bi
-                mma_tf32(t_re, a2, b3, id_ii, 1u);
-                mma_tf32(t_re, a3, b2, id_ii, 1u);
-                mma_tf32(t_im, a0, b2, id_ri, first);       // Ar Bi
-                mma_tf32(t_im, a0, b3, id_ri, 1u);
-                mma_tf32(t_im, a1, b2, id_ri, 1u);
-                mma_tf32(t_im, a2, b0, id_ir, 1u);          // Ai Br
-                mma_tf32(t_im, a2, b1, id_ir, 1u);
-                mma_tf32(t_im, a3, b0, id_ir, 1u);
-            }
-            mma_commit(mb0 + 8 * (s & 1));
+            const uint32_t sa = sbase + buf * TC_STAGE, sb = sa + 4 * TC_PLANE_A;
+            const uint64_t a0 = smem_desc(sa), a1 = smem_desc(sa + TC_PLANE_A), a2 = smem_desc(sa + 2 * TC_PLANE_A),
+                           a3 = smem_desc(sa + 3 * TC_PLANE_A);
+            const uint64_t b0 = smem_desc(sb), b1 = smem_desc(sb + TC_PLANE_B), b2 = smem_desc(sb + 2 * TC_PLANE_B),
+                           b3 = smem_desc(sb + 3 * TC_PLANE_B);
+            const uint32_t first = (s == 0) ? 0u : 1u;
+            mma_tf32(t_re, a0, b0, id_pos, first);      // Ar Br
+            mma_tf32(t_re, a0, b1, id_pos, 1u);
+            mma_tf32(t_re, a1, b0, id_pos, 1u);
+            mma_tf32(t_re, a2, b2, id_neg, 1u);         // - Ai Bi
+            mma_tf32(t_re, a2, b3, id_neg, 1u);
+            mma_tf32(t_re, a3, b2, id_neg, 1u);
+            mma_tf32(t_im, a0, b2, id_pos, first);      // Ar Bi
+            mma_tf32(t_im, a0, b3, id_pos, 1u);
+            mma_tf32(t_im, a1, b2, id_pos, 1u);
+            mma_tf32(t_im, a2, b0, id_pos, 1u);         // Ai Br
+            mma_tf32(t_im, a2, b1, id_pos, 1u);
+            mma_tf32(t_im, a3, b0, id_pos, 1u);
+            mma_commit(mb0 + 8 * buf);
         }
         if (s + 1 < nst) {
-            if (ok && s >= 1 && !mbar_wait(mb0 + 8 * ((s - 1) & 1), ((s - 1) >> 1) & 1)) ok = false;
-            store((s + 1) & 1, ra, rb);
-            if (s + 3 < nst) load(kbeg + TC_BK * (s + 3), ra, rb);
+            const int p = s - 2;                        // last stage that used buffer (s + 1) % 3
+            if (ok && p >= 0 && !mbar_wait(mb0 + 8 * (p % TC_NSTAGE), (p / TC_NSTAGE) & 1)) ok = false;
+            store((s + 1) % TC_NSTAGE);
+            if (s + 2 < nst) load(kbeg + TC_BK * (s + 2));
         }
-    };
-    load(kbeg, ra0, rb0);
-    store(0, ra0, rb0);
-    if (nst > 1) load(kbeg + TC_BK, ra1, rb1);          // stage 1 -> set 1
-    if (nst > 2) load(kbeg + 2 * TC_BK, ra0, rb0);      // stage 2 -> set 0
-    for (int s = 0; s < nst; s += 2) {
-        step(s, ra1, rb1);                              // stores stage s + 1 (odd) from set 1
-        if (s + 1 < nst) step(s + 1, ra0, rb0);         // stores stage s + 2 (even) from set 0
     }
-    if (ok && !mbar_wait(mb0 + 8 * ((nst - 1) & 1), ((nst - 1) >> 1) & 1)) ok = false;
+    {
+        const int p = nst - 1;                          // its commit covers every earlier MMA
+        if (ok && !mbar_wait(mb0 + 8 * (p % TC_NSTAGE), (p / TC_NSTAGE) & 1)) ok = false;
+    }
     fence_after_sync();
     ok = __syncthreads_and(ok);
 

@@ -301,7 +301,7 @@ void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops)
     }
     bool tc = false;
     if constexpr (sizeof(T) == 4) {
-        tc = (g.bn == 256);
+        tc = (g.bm == 128 && g.bn == 128);
         if (tc)
             launch_gemm_tc(g, grid, st);
         else if (g.bm == G2_BM)

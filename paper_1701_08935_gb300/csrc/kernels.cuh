@@ -6,7 +6,7 @@ namespace zolo {
 
 template <class T> struct GemmArgs {
     int bm;                              // tile height of this launch (64, or 128 for complex64)
-    int bn;                              // tile width: 64, or 256 for the complex64 tensor-core kernel
+    int bn;                              // tile width: 64 or 128 (bm = bn = 128: complex64 tensor cores)
     const GJob *jobs[MAX_INST];
     const int32_t *tmap[MAX_INST];       // job of every tile of the launch, or null (binary search)
     int njobs[MAX_INST];
@@ -117,7 +117,7 @@ void prof_set(int mask);          // bit 0: complex64 GEMMs, bit 1: complex128 G
 double prof_collect_ms();          // synchronises the recorded events, returns the summed time
                                    // (and adds the tensor-core share to counters().tc_*)
 template <class T> void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops = 0.0);
-// complex64 tcgen05 GEMM (tiles 128 x <= 256, bm = 128, bn = 256 in the job tiling)
+// complex64 tcgen05 GEMM (tiles 128 x <= 128, bm = bn = 128 in the job tiling)
 void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st);
 // device status word of the tensor-core GEMM: 0, or ZOLO_ETIMEOUT after an expired
 // mbarrier wait (ZOLO_ECUDA when it cannot be read); `reset` clears a non-zero word
