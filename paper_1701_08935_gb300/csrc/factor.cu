@@ -1004,7 +1004,8 @@ int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, i
     return ZOLO_OK;
 }
 
-int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st) {
+int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st,
+                const float2 *Xs) {
     // GX = const_hat X + sum_j ( w_hat_j K_j^-1 B X + conj(w_hat_j) K_j^-H B X )   (eq. solve)
     const int r1 = h->r1;
     const int nblk = 1 + 2 * r1;
@@ -1012,7 +1013,10 @@ int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
     int rc = ensure_scratch(h, k, nblk, &scr);
     if (rc) return rc;
     c128 *BX = scr;
-    launch_spmm(h->B, k, X, ldx, BX, k, c128{1.0, 0.0}, false, st);
+    if (Xs && (h->B.vrdf || h->B.vdf))
+        launch_spmm_df(h->B, k, Xs, BX, st);
+    else
+        launch_spmm(h->B, k, X, ldx, BX, k, c128{1.0, 0.0}, false, st);
     for (int p0 = 0; p0 < 2 * r1; p0 += MAX_INST) {
         const int ni = std::min(MAX_INST, 2 * r1 - p0);
         int pole[MAX_INST], herm[MAX_INST];

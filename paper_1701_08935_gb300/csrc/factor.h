@@ -129,7 +129,11 @@ int solve_refined(zolo_factor_s *h, int ninst, const int *pole, const int *herm,
                   int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st, int *n_refine);
 int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
                 int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st, int *n_refine);
-int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st);
+// Y = G X (eq. solve).  When Xs (the double-float planes of X: n k float2 hi parts, then
+// n k remainders, ld = k) is given and the pencil has double-float values, B X is formed
+// from them on the FP32 pipe.
+int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st,
+                const float2 *Xs = nullptr);
 // scratch block of complex128 with at least `blocks` n x k blocks
 int ensure_scratch(zolo_factor_s *h, int64_t k, int blocks, c128 **out);
 }  // namespace zolo

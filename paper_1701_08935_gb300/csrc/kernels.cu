@@ -725,6 +725,43 @@ void launch_refine_resid_df(const DevCSR &A, const DevCSR &M, const ResidDfArgs 
     g_counters.launches++;
 }
 
+__global__ void __launch_bounds__(256) k_spmm_df(DevCSR M, int k, const float2 *__restrict__ Xs,
+                                                 c128 *__restrict__ Y) {
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= M.n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = M.rp[row], e = M.rp[row + 1], nk = M.n * k;
+    for (int c = lane; c < k; c += 32) {
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        if (M.vrdf) {
+            for (int64_t p = b; p < e; ++p) {
+                const float2 a = M.vrdf[p];
+                const int64_t x = (int64_t)M.ci[p] * k + c;
+                const float2 xh = Xs[x], xl = Xs[nk + x];
+                df_fma(rh, rl, a.x, a.y, xh.x, xl.x);
+                df_fma(ih, il, a.x, a.y, xh.y, xl.y);
+            }
+        } else {
+            for (int64_t p = b; p < e; ++p) {
+                const float4 a = M.vdf[p];
+                const int64_t x = (int64_t)M.ci[p] * k + c;
+                const float2 xh = Xs[x], xl = Xs[nk + x];
+                df_fma(rh, rl, a.x, a.y, xh.x, xl.x);             // ar xr
+                df_fma(rh, rl, -a.z, -a.w, xh.y, xl.y);           // - ai xi
+                df_fma(ih, il, a.x, a.y, xh.y, xl.y);             // ar xi
+                df_fma(ih, il, a.z, a.w, xh.x, xl.x);             // ai xr
+            }
+        }
+        Y[row * k + c] = mk<double>(df_widen(rh) + df_widen(rl), df_widen(ih) + df_widen(il));
+    }
+}
+
+void launch_spmm_df(const DevCSR &M, int64_t k, const float2 *Xs, c128 *Y, cudaStream_t st) {
+    if (M.n == 0 || k == 0) return;
+    k_spmm_df<<<(unsigned)((M.n + 7) / 8), 256, 0, st>>>(M, (int)k, Xs, Y);
+    g_counters.launches++;
+}
+
 __global__ void k_split_df(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx, float4 *__restrict__ Xs) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * k) return;

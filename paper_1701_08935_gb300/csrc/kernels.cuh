@@ -88,6 +88,9 @@ struct ResidDfArgs {
     int64_t ldb, ldr;
 };
 void launch_refine_resid_df(const DevCSR &A, const DevCSR &M, const ResidDfArgs &r, cudaStream_t st);
+// Y = M X with X given as double-float planes (n k float2 hi parts, then n k remainders,
+// ld = k), in df64 on the FP32 pipe; Y (n x k, ld = k) gets FP64 values.
+void launch_spmm_df(const DevCSR &M, int64_t k, const float2 *Xs, c128 *Y, cudaStream_t st);
 // Xs[i k + c] = double-float split of X[i ldx + c] (n x k)
 void launch_split_df(int64_t n, int64_t k, const c128 *X, int64_t ldx, float4 *Xs, cudaStream_t st);
 

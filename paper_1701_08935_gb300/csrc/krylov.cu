@@ -616,7 +616,7 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
         }
         k_from_planes<<<nblk(blk), 256, 0, st>>>(n, (int)k, plane(i), Vc);
         count_launch();
-        rc = apply_inner(h, k, Vc, k, Wv, k, st);
+        rc = apply_inner(h, k, Vc, k, Wv, k, st, plane(i));
         if (rc) {                                          // a failed inner solve is not a short GMRES
             h->inner_failed = true;
             return rc;
