@@ -8,13 +8,14 @@
 // Arithmetic: every complex64 operand x is split into two TF32 numbers, x = hi + lo with
 // hi = x rounded to 11 significant bits and lo = (x - hi) rounded the same way (3xTF32:
 // the products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor memory, the
-// lo*lo term of relative size 2^-22 is dropped).  A complex product takes four real
-// products, so one k-step of 8 issues 12 MMAs of 128 x w x 8:
+// lo*lo term, at most 2^-24 of the product, is dropped).  A complex product takes four
+// real products, so one k-step of 8 issues 12 MMAs of 128 x w x 8:
 //      Cr += Ar Br - Ai Bi,  Ci += Ar Bi + Ai Br        (each real product: 3 MMAs)
 // with the minus taken by the instruction descriptor's negate-A bit (conjugated operands
-// are conjugated while they are staged).  The result is as
-// accurate as the FP32 SIMT kernels up to a small factor; the FP64 refinement of every
-// mixed-precision solve absorbs the difference.
+// are conjugated while they are staged).  The tensor core's FP32 accumulation truncates, so
+// products are ~5-10x less accurate than with FP32 FMAs (~1e-6 relative at k = 64); the FP64
+// refinement of every mixed-precision solve absorbs this (the same number of refinement
+// steps was measured either way).
 //
 // Tiles: one CTA per 128 x w tile of C, w <= 128 columns chosen per job so that the
 // ceil(n / 128) column tiles have equal width (a multiple of 16).  Two CTAs share an SM, so
