@@ -6,9 +6,10 @@
 //
 // Every operation uses the _rn intrinsics so that the compiler cannot contract a product
 // and a sum into an FMA (which would break the error-free transformations).  The
-// conversions from and to FP64 work on the bit patterns with integer operations only;
-// they are exact for finite values whose magnitude is in the normal float range
-// (|x| >= 2^-126), and flush smaller magnitudes to zero.
+// conversions from and to FP64 work on the bit patterns with integer operations only.
+// df_split gives x = hi + lo to 2^-46 relative for finite 2^-80 <= |x| < 2^128; for
+// smaller |x| a remainder below the normal float range is flushed (absolute error < 2^-126,
+// and |x| < 2^-126 splits to zero).  df_widen is exact for normal floats and zero.
 #pragma once
 
 #include <cstdint>
@@ -60,8 +61,8 @@ __host__ __device__ __forceinline__ int df_clz32(uint32_t v) {
 #endif
 }
 
-// x = hi + lo exactly (up to the flush of |lo| < 2^-126): hi keeps the top 24 bits of the
-// mantissa (truncated), lo the next 24 of the remaining 29.
+// x = hi + lo (up to the flush of |lo| < 2^-126): hi keeps the top 24 bits of the mantissa
+// (truncated), lo the leading 24 of the remaining 29 (truncated).
 __host__ __device__ __forceinline__ void df_split(double x, float &hi, float &lo) {
     const uint64_t u = df_d2u(x);
     const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
