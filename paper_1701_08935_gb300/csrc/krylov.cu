@@ -35,7 +35,8 @@ constexpr int JT = 8;             // basis vectors per pass of the multi-dot ker
 // part[b][j][c] = sum over rows i = b, b+G, ... of conj(V_j[i,c]) W[i,c], j in [j0, j0+nj)
 // FP64 -> FP32 by integer operations on the bit pattern (truncating the mantissa; values
 // below 2^-126 become 0), so that reading FP64 operands costs no FP64-pipe instructions,
-// which GB300 issues at ~1/64 of the FP32 rate.  Finite inputs only.
+// which GB300 issues at ~1/64 of the FP32 rate.  Finite |x| < 2^128 only (the Krylov
+// vectors it reads are normalised).
 __device__ __forceinline__ float f64_to_f32_trunc(double x) {
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
     const int32_t t = (int32_t)(hi & 0x7FFFFFFFu) - (int32_t)(896u << 20);    // rebias 1023 -> 127
