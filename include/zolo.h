@@ -107,8 +107,9 @@ typedef struct {
 /* Options.  zolo_opts_default() fills the documented defaults. */
 typedef struct {
     int32_t  grid[3];      /* grid dims for geometric nested dissection (vertex id
-                              x + nx (y + ny z)); grid[0] <= 0: no geometry, a single
-                              dense front (only for n <= 8192)                  */
+                              x + nx (y + ny z)); grid[0] <= 0: no geometry, nested
+                              dissection by level structures of the pattern's graph
+                              (George & Liu)                                    */
     int32_t  leaf_max;     /* nested-dissection leaf size (default 32)            */
     int32_t  precision;    /* ZOLO_PREC_FP64 (default) or ZOLO_PREC_MIXED         */
     int32_t  gmres_m_max;  /* GMRES steps at most (default 100)                   */

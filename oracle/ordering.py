@@ -24,6 +24,8 @@ sorted increasingly; the front's rows are pivots(s) followed by U(s).  A pattern
 edge that joins two subtrees of the separator tree (a stencil wider than the
 nearest neighbours) breaks the dissection; it is reported as an error.
 """
+import collections
+
 import numpy as np
 
 
@@ -84,6 +86,105 @@ def nd_grid(dims, leaf_max=32):
 
     rec([(0, nx), (0, ny), (0, nz)])
     return Tree(np.concatenate(perm), first, npiv, parent)
+
+
+def nd_graph(pattern, leaf_max=32):
+    """Graph nested dissection by level structures (George & Liu), for pencils given
+    without grid geometry.  On the symmetric pattern (self-loops ignored), a vertex set S
+    is ordered as follows:
+      * its connected components (in the subgraph induced by S) are ordered by their
+        smallest vertex and become sibling subtrees;
+      * a component C with at most ``leaf_max`` vertices is a leaf front (ascending vertex
+        index);
+      * otherwise a pseudo-peripheral root r is found: start at min(C); BFS gives levels;
+        take the vertex of smallest degree in C on the last level (lowest index on ties);
+        if its BFS has more levels, it becomes r and the step repeats, else r stays;
+      * with the h levels L_0..L_{h-1} of the BFS from r: if h < 3 the component is a leaf
+        front; otherwise the middle level L_{h//2} (ascending) is the separator front, whose
+        children are the subtrees of L_0..L_{h//2-1} and of L_{h//2+1}..L_{h-1}, ordered first
+        (in that order).  Edges join adjacent levels only, so the two parts are disconnected.
+    Nodes are numbered in completion order (children before parents); a disconnected
+    pattern gives several roots."""
+    P = pattern.tocsr()
+    n = P.shape[0]
+    nbr = []
+    for v in range(n):
+        cols = P.indices[P.indptr[v]:P.indptr[v + 1]]
+        nbr.append(sorted(int(c) for c in set(cols.tolist()) if c != v))
+    perm, first, npiv, parent = [], [], [], []
+    count = [0]
+
+    def emit(verts):
+        node = len(first)
+        first.append(count[0]); npiv.append(len(verts)); parent.append(-1)
+        perm.append(np.asarray(verts, dtype=np.int32)); count[0] += len(verts)
+        return node
+
+    def bfs(inset, root):
+        seen = {root}
+        levels = [[root]]
+        while True:
+            nxt = set()
+            for v in levels[-1]:
+                for u in nbr[v]:
+                    if u in inset and u not in seen:
+                        nxt.add(u)
+            if not nxt:
+                return levels
+            seen |= nxt
+            levels.append(sorted(nxt))
+
+    def components(verts):
+        inset = set(verts)
+        left = set(verts)
+        comps = []
+        for v in sorted(verts):
+            if v not in left:
+                continue
+            comp = set()
+            stack = [v]
+            left.discard(v)
+            while stack:
+                x = stack.pop()
+                comp.add(x)
+                for u in nbr[x]:
+                    if u in left:
+                        left.discard(u)
+                        stack.append(u)
+            comps.append(sorted(comp))
+        return comps
+
+    def rec_set(verts):
+        return [rec_connected(c) for c in components(verts)]
+
+    def rec_connected(comp):
+        if len(comp) <= leaf_max:
+            return emit(comp)
+        inset = set(comp)
+        r = comp[0]
+        levels = bfs(inset, r)
+        while True:
+            deg = lambda v: sum(1 for u in nbr[v] if u in inset)
+            cand = min(levels[-1], key=lambda v: (deg(v), v))
+            lv = bfs(inset, cand)
+            if len(lv) > len(levels):
+                r, levels = cand, lv
+            else:
+                break
+        h = len(levels)
+        if h < 3:
+            return emit(comp)
+        m = h // 2
+        part1 = sorted(v for L in levels[:m] for v in L)
+        part2 = sorted(v for L in levels[m + 1:] for v in L)
+        kids = rec_set(part1) + rec_set(part2)
+        node = emit(levels[m])
+        for k in kids:
+            parent[k] = node
+        return node
+
+    rec_set(list(range(n)))
+    return Tree(np.concatenate(perm) if perm else np.zeros(0, np.int32), first, npiv, parent)
 
 
 class Symbolic:

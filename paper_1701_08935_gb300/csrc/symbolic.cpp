@@ -1,8 +1,9 @@
 // Ordering and symbolic analysis (host, once per sparsity pattern).
 //
 // The multifrontal method (Section 2.3, "fast direct solvers") factors each shifted
-// matrix front by front along an assembly tree.  The tree here is the separator tree
-// of a geometric nested dissection of the grid the pencil lives on:
+// matrix front by front along an assembly tree: the separator tree of a nested
+// dissection, by level structures on the pattern's graph when no grid is given (see
+// GNDBuilder), else geometric on the grid the pencil lives on:
 //   * a box with at most leaf_max vertices is one front (lexicographic, x fastest);
 //   * otherwise the longest axis (x before y before z on ties) is split at the plane
 //     lo + d/2; the lower box, the upper box and then the plane are ordered, the
@@ -74,6 +75,144 @@ struct NDBuilder {
     }
 };
 
+// Graph nested dissection by level structures (George & Liu) for pencils without grid
+// geometry, on the union pattern of A and B (self-loops ignored).  A vertex set is split
+// into its connected components (ordered by smallest vertex, sibling subtrees); a
+// component of at most leaf_max vertices is a leaf front (ascending index); otherwise a
+// pseudo-peripheral root is found (start at the smallest vertex; repeatedly BFS from the
+// last level's vertex of smallest degree in the component, lowest index on ties, while that
+// adds levels), and with the BFS levels L_0..L_{h-1} from it the middle level L_{h/2} is
+// the separator front (h < 3: leaf), after the subtrees of the levels before it and of the
+// levels after it.  Edges only join adjacent levels, so the two parts are disconnected.
+struct GNDBuilder {
+    int leaf_max = 32;
+    std::vector<int64_t> aptr;           // adjacency (sorted, no self-loops)
+    std::vector<int32_t> adj;
+    std::vector<int32_t> perm, first, npiv, parent;
+    int32_t count = 0;
+    std::vector<int32_t> in_set, seen;   // stamps: membership of the current set, visits
+    int32_t set_stamp = 0, seen_stamp = 0;
+
+    void build_adjacency(const zolo_csr *A, const zolo_csr *B) {
+        const int64_t n = A->n;
+        aptr.assign(n + 1, 0);
+        adj.clear();
+        std::vector<int32_t> row;
+        for (int64_t v = 0; v < n; ++v) {
+            row.clear();
+            for (int64_t p = A->row_ptr[v]; p < A->row_ptr[v + 1]; ++p)
+                if (A->col_idx[p] != v) row.push_back(A->col_idx[p]);
+            for (int64_t p = B->row_ptr[v]; p < B->row_ptr[v + 1]; ++p)
+                if (B->col_idx[p] != v) row.push_back(B->col_idx[p]);
+            std::sort(row.begin(), row.end());
+            row.erase(std::unique(row.begin(), row.end()), row.end());
+            adj.insert(adj.end(), row.begin(), row.end());
+            aptr[v + 1] = (int64_t)adj.size();
+        }
+        in_set.assign(n, 0);
+        seen.assign(n, 0);
+    }
+    int emit(const std::vector<int32_t> &verts) {
+        const int node = (int)first.size();
+        first.push_back(count);
+        npiv.push_back((int32_t)verts.size());
+        parent.push_back(-1);
+        perm.insert(perm.end(), verts.begin(), verts.end());
+        count += (int32_t)verts.size();
+        return node;
+    }
+    // BFS levels (each sorted) of the current set from root
+    void bfs(int32_t root, std::vector<std::vector<int32_t>> &levels) {
+        const int32_t sv = ++seen_stamp, st = set_stamp;
+        levels.assign(1, std::vector<int32_t>(1, root));
+        seen[root] = sv;
+        for (;;) {
+            std::vector<int32_t> nxt;
+            for (int32_t v : levels.back())
+                for (int64_t p = aptr[v]; p < aptr[v + 1]; ++p) {
+                    const int32_t u = adj[p];
+                    if (in_set[u] == st && seen[u] != sv) {
+                        seen[u] = sv;
+                        nxt.push_back(u);
+                    }
+                }
+            if (nxt.empty()) return;
+            std::sort(nxt.begin(), nxt.end());
+            levels.push_back(std::move(nxt));
+        }
+    }
+    int degree_in_set(int32_t v) const {
+        int d = 0;
+        for (int64_t p = aptr[v]; p < aptr[v + 1]; ++p) d += (in_set[adj[p]] == set_stamp);
+        return d;
+    }
+    // subtrees of a sorted vertex set, one per connected component; returns their roots
+    void rec_set(const std::vector<int32_t> &verts, std::vector<int> &roots) {
+        const int32_t st = ++set_stamp;
+        for (int32_t v : verts) in_set[v] = st;
+        const int32_t sv = ++seen_stamp;
+        std::vector<std::vector<int32_t>> comps;
+        std::vector<int32_t> stack;
+        for (int32_t v : verts) {
+            if (seen[v] == sv) continue;
+            std::vector<int32_t> comp;
+            seen[v] = sv;
+            stack.assign(1, v);
+            while (!stack.empty()) {
+                const int32_t x = stack.back();
+                stack.pop_back();
+                comp.push_back(x);
+                for (int64_t p = aptr[x]; p < aptr[x + 1]; ++p) {
+                    const int32_t u = adj[p];
+                    if (in_set[u] == st && seen[u] != sv) {
+                        seen[u] = sv;
+                        stack.push_back(u);
+                    }
+                }
+            }
+            std::sort(comp.begin(), comp.end());
+            comps.push_back(std::move(comp));
+        }
+        for (auto &c : comps) roots.push_back(rec_connected(c));
+    }
+    int rec_connected(const std::vector<int32_t> &comp) {
+        if ((int64_t)comp.size() <= leaf_max) return emit(comp);
+        const int32_t st = ++set_stamp;
+        for (int32_t v : comp) in_set[v] = st;
+        std::vector<std::vector<int32_t>> levels, lv;
+        bfs(comp[0], levels);
+        for (;;) {
+            int32_t cand = -1;
+            int cd = 0;
+            for (int32_t v : levels.back()) {          // ascending: the first minimum wins ties
+                const int d = degree_in_set(v);
+                if (cand < 0 || d < cd) {
+                    cand = v;
+                    cd = d;
+                }
+            }
+            bfs(cand, lv);
+            if (lv.size() > levels.size()) levels.swap(lv);
+            else break;
+        }
+        const int h = (int)levels.size();
+        if (h < 3) return emit(comp);
+        const int m = h / 2;
+        std::vector<int32_t> part1, part2;
+        for (int L = 0; L < m; ++L) part1.insert(part1.end(), levels[L].begin(), levels[L].end());
+        for (int L = m + 1; L < h; ++L) part2.insert(part2.end(), levels[L].begin(), levels[L].end());
+        std::sort(part1.begin(), part1.end());
+        std::sort(part2.begin(), part2.end());
+        std::vector<int32_t> sep = levels[m];
+        std::vector<int> kids;
+        rec_set(part1, kids);
+        rec_set(part2, kids);
+        const int node = emit(sep);
+        for (int k : kids) parent[k] = node;
+        return node;
+    }
+};
+
 double sum_sq(double x) { return x * (x + 1.0) * (2.0 * x + 1.0) / 6.0; }   // 0^2 + ... + x^2
 
 }  // namespace
@@ -127,12 +266,18 @@ int analyze(const zolo_csr *A, const zolo_csr *B, const zolo_opts &opts, zolo_sy
         S.npiv.swap(nd.npiv);
         S.parent.swap(nd.parent);
     } else {
-        if (n > 8192) return set_error(ZOLO_EINVAL, "no grid geometry given: single dense front needs n <= 8192");
-        S.perm.resize(n);
-        for (int64_t i = 0; i < n; ++i) S.perm[i] = (int32_t)i;
-        S.first.assign(1, 0);
-        S.npiv.assign(1, (int32_t)n);
-        S.parent.assign(1, -1);
+        GNDBuilder nd;
+        nd.leaf_max = opts.leaf_max > 0 ? opts.leaf_max : 32;
+        nd.build_adjacency(A, B);
+        nd.perm.reserve(n);
+        std::vector<int32_t> all(n);
+        for (int64_t i = 0; i < n; ++i) all[i] = (int32_t)i;
+        std::vector<int> roots;
+        nd.rec_set(all, roots);
+        S.perm.swap(nd.perm);
+        S.first.swap(nd.first);
+        S.npiv.swap(nd.npiv);
+        S.parent.swap(nd.parent);
     }
     const int32_t nn = (int32_t)S.first.size();
     S.nnodes = nn;

@@ -86,3 +86,20 @@ def test_refactor_is_repeatable():
     # the factorisation is deterministic; the solves split long inner products over
     # CTAs with atomic adds, so results agree to rounding
     assert colrel(X2, X1) < 1e-13
+
+
+@pytest.mark.parametrize("name", ["real2d_40", "cplx3d_12"])
+@pytest.mark.parametrize("prec", [Z.PREC_FP64, Z.PREC_MIXED])
+def test_graph_nd_factor_solves(name, prec):
+    """Pencils given without grid geometry: graph nested dissection (level structures of
+    the pattern), then the same multifrontal factorisation and solves, against SuperLU."""
+    need_gpu()
+    pen, leaf, gaps, _ = case(name)
+    flt = Z.Filter(*gaps, 2, 2)
+    fac = Z.Factor(pen.A, pen.B, flt, opts=Z.default_opts(leaf_max=leaf, precision=prec))
+    Bk = synth.random_block(pen.n, 33, 8)
+    for j, s in enumerate(flt.sigma_hat):
+        ref = FA.Solver(pen.A, pen.B, s)
+        for herm in (False, True):
+            X = host(fac.solve(j, dev(Bk), herm=herm))
+            assert colrel(X, ref.solve(Bk, herm=herm)) < 1e-10, (j, herm)

@@ -106,3 +106,54 @@ def test_union_pattern_of_config2_recipe_is_27_point():
     Q = _stencil_pattern((6, 6, 6), True)
     assert (P != 0).sum() == (Q != 0).sum()
     assert abs((P != 0).astype(int) - (Q != 0).astype(int)).sum() == 0
+
+
+# ---------------------------------------------------------------- graph nested dissection
+def test_graph_nd_hand_derived_path():
+    """Path 0-1-...-6, leaf_max 1.  BFS from 0 has 7 levels and the BFS from the far end 6
+    has no more, so the root stays 0: separator {3}; the left part 0-1-2 has root 0 and
+    separator {1}, the right part 4-5-6 has root 4 and separator {5}.  Completion order:
+    0, 2, 1, 4, 6, 5, 3."""
+    n = 7
+    P = sp.diags([np.ones(n - 1), np.ones(n - 1)], [-1, 1], shape=(n, n)).tocsr()
+    t = O.nd_graph(P, leaf_max=1)
+    assert t.perm.tolist() == [0, 2, 1, 4, 6, 5, 3]
+    assert t.first.tolist() == list(range(7)) and t.npiv.tolist() == [1] * 7
+    assert t.parent.tolist() == [2, 2, 6, 5, 5, 6, -1]
+
+
+@pytest.mark.parametrize("dims,full,leaf", [((7, 9), False, 4), ((6, 5), True, 3),
+                                            ((5, 4, 6), False, 8), ((3, 3, 3), True, 1)])
+def test_graph_nd_update_rows_equal_brute_force_fill(dims, full, leaf):
+    """Graph ND of a stencil pattern (no geometry): the fronts' update rows are exactly the
+    fill of a boolean elimination in the same order."""
+    P = _stencil_pattern(dims, full)
+    t = O.nd_graph(P, leaf_max=leaf)
+    S = O.Symbolic(t, P)
+    Q = _brute_force_structure(P, t.perm)
+    for s in range(t.nnodes):
+        f, e = int(t.first[s]), int(t.first[s] + t.npiv[s])
+        true_rows = np.nonzero(Q[e:, f:e].any(axis=1))[0] + e
+        assert S.U[s].tolist() == true_rows.tolist()
+
+
+def test_graph_nd_tree_invariants_on_random_graphs():
+    rng = np.random.default_rng(11)
+    for trial in range(5):
+        n = int(rng.integers(50, 400))
+        pts = rng.random((n, 2))
+        d = np.sqrt(((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1))
+        P = sp.csr_matrix((d < 1.6 / np.sqrt(n)) & (d > 0)).astype(float)
+        t = O.nd_graph(P, leaf_max=int(rng.integers(1, 20)))
+        assert sorted(t.perm.tolist()) == list(range(n))
+        assert np.all((t.parent == -1) | (t.parent > np.arange(t.nnodes)))
+        assert np.all(np.diff(t.first) == t.npiv[:-1]) and t.first[0] == 0
+        O.Symbolic(t, P + sp.identity(n))          # separator property: raises if violated
+        # a separator is never larger than the set it splits
+        sizes = np.zeros(t.nnodes, dtype=int)
+        for s in range(t.nnodes):
+            sizes[s] += t.npiv[s]
+            if t.parent[s] >= 0:
+                sizes[t.parent[s]] += sizes[s]
+        inner = [s for s in range(t.nnodes) if sizes[s] > t.npiv[s]]
+        assert all(t.npiv[s] < sizes[s] for s in inner)
