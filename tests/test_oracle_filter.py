@@ -199,3 +199,21 @@ def test_six_factorizations_reach_machine_accuracy():
     assert f.delta0 < 1e-15
     g = F.ZoloFilter(-1.005, -0.995, 0.995, 1.005, 2, 2)
     assert g.delta0 > 1e-6          # a low order is visibly worse
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 5])
+@pytest.mark.parametrize("ell", [1e-3, 0.05, 0.3, 0.9])
+def test_zolo_c_reflection_identities(r, ell):
+    """c_j of Theorem 1 from sn/cn at u_j = j K'/(2r): since sn(K' - u) = cn(u)/dn(u) and
+    cn(K' - u) = l sn(u)/dn(u) (modulus l'), c_j c_{2r-j} = l^2 and c_r = l; the c_j increase
+    with j (sn/cn increases on (0, K'))."""
+    c = F.zolo_c(r, ell)
+    assert len(c) == 2 * r - 1
+    assert c[r - 1] == pytest.approx(ell, rel=1e-12)
+    for j in range(1, 2 * r):
+        assert c[j - 1] * c[2 * r - j - 1] == pytest.approx(ell * ell, rel=1e-11)
+    assert all(c[i] < c[i + 1] for i in range(len(c) - 1))
+    # the product form is odd and positive on (0, 1]
+    x = np.linspace(1e-3, 1.0, 50)
+    assert np.all(F.zolo_product(x, c) > 0)
+    assert np.allclose(F.zolo_product(-x, c), -F.zolo_product(x, c), rtol=0, atol=1e-15)
