@@ -93,10 +93,10 @@ thread_local std::vector<int32_t> *g_plan_tmap = nullptr;
 constexpr double TC_MIN_ROWS = 128.0;
 
 // Append a launch of GEMM jobs (empty products dropped) and return its descriptor.
-// Complex64 launches whose jobs average >= TC_MIN_ROWS rows run on the tensor-core kernel
-// (128 x <= 128 tiles; every complex64 launch with ZOLO_TC_ALWAYS, none with ZOLO_TC_OFF,
-// where they take 128 x 64 FP32 tiles instead); other launches take 64 x 64 tiles (32 x 128
-// when the jobs average <= 40 rows).  With allow_split, a launch with fewer than ~4 waves
+// Tiles of a complex64 launch: the tensor-core kernel (128 x <= 128) when its jobs average
+// >= TC_MIN_ROWS rows (every launch with ZOLO_TC_ALWAYS, none with ZOLO_TC_OFF); otherwise
+// FP32-FMA tiles of 128 x 64 when they average >= 256 rows, 32 x 128 when <= 40, else
+// 64 x 64.  Complex128 launches take 64 x 64.  With allow_split, a launch with fewer than ~4 waves
 // of tiles splits the kk extent of its accumulating jobs (GJ_SUB / GJ_ACC, kk >= 512) over
 // several CTAs (atomic adds).
 Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool allow_split = false) {
