@@ -90,7 +90,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- workload
 def make_workload(case="full"):
-    from paper_1701_08935_gb300 import synth
+    import synth
     if case == "small":
         return synth.pencil_3d_peierls(32, seed=SEED, wells=4)
     return synth.pencil_3d_peierls(N_SIDE, seed=SEED)
@@ -371,7 +371,7 @@ def cpu_sample():
     """A bounded sample of the workload for the CPU oracle: the same recipe on a 12^3 grid
     (4 wells), the 20 eigenvalues 11..30, r = (2, 6), subspace 30, Algorithm 1 with the
     hybrid Algorithm 2 as the filter (interval placed from the oracle's dense spectrum)."""
-    from paper_1701_08935_gb300 import synth
+    import synth
     from oracle import eigs as E
     pen = synth.pencil_3d_peierls(12, seed=SEED, wells=4)
     lam, _ = E.dense_eigs(pen.A, pen.B)
@@ -382,7 +382,7 @@ def cpu_baseline(steps=1):
     from oracle import apply as AP
     from oracle import eigs as E
     from oracle import filter as F
-    from paper_1701_08935_gb300 import synth
+    import synth
     pen, lam = cpu_sample()
     lo, hi = 10, 30
     gaps = (lam[lo - 1], lam[lo], lam[hi - 1], lam[hi])       # eigengaps at the true eigenvalues

@@ -14,9 +14,9 @@
  * Conventions shared by every entry point
  *  - Every function returns an int status (ZOLO_OK = 0); nothing throws across the
  *    ABI.  zolo_last_error() gives a thread-local message for the last failure.
- *  - Matrices enter as host CSR (zolo_csr): 0-based, n x n, full pattern (both
- *    triangles), column indices sorted inside each row; the library copies what it
- *    keeps, the caller keeps ownership of its arrays.
+ *  - Matrices enter as CSR (zolo_csr), in host or device memory: 0-based, n x n, full
+ *    pattern (both triangles), column indices sorted inside each row; the library
+ *    copies what it keeps, the caller keeps ownership of its arrays.
  *  - Vector blocks are DEVICE arrays of complex double (interleaved re, im) laid out
  *    row-major: entry (i, c) of an n x k block sits at X[i*ld + c], ld >= k (a
  *    contiguous torch tensor of shape (n, k) has ld = k).  Rows use the caller's
@@ -49,6 +49,19 @@ extern "C" {
 /* ---- value types of CSR arrays ------------------------------------------ */
 #define ZOLO_R64  1       /* double */
 #define ZOLO_C128 2       /* complex double, interleaved (re, im) */
+#define ZOLO_C64  3       /* complex float, interleaved (re, im); widened to complex double */
+
+/* ---- where the CSR arrays live ------------------------------------------- */
+#define ZOLO_HOST   0     /* host memory (default) */
+#define ZOLO_DEVICE 1     /* device memory of the current GPU: the library copies the arrays
+                             to the host once per call (the ordering and the symbolic
+                             analysis run there) and keeps its own device copy */
+
+/* ---- filter kinds --------------------------------------------------------- */
+#define ZOLO_FILTER_ZOLO 0  /* the composite Zolotarev filter R_ab (eq. R2), Algorithm 2      */
+#define ZOLO_FILTER_CITZ 1  /* contour integral (eq. contourintegral) on the circle through a
+                               and b, trapezoidal rule (Section 1.1): factored poles only   */
+#define ZOLO_FILTER_CIGQ 2  /* the same contour, Gauss-Legendre rule on each half circle   */
 
 /* ---- arithmetic of the factorisation and solves ------------------------- */
 #define ZOLO_PREC_FP64  0 /* complex128 everywhere */
@@ -68,18 +81,21 @@ extern "C" {
 typedef struct {
     int64_t        n;        /* rows = columns */
     int64_t        nnz;
-    const int64_t *row_ptr;  /* n+1 entries, host */
-    const int32_t *col_idx;  /* nnz entries, host, sorted within each row */
-    const void    *val;      /* nnz values of type `dtype`, host */
-    int32_t        dtype;    /* ZOLO_R64 or ZOLO_C128 */
-    int32_t        reserved;
+    const int64_t *row_ptr;  /* n+1 entries */
+    const int32_t *col_idx;  /* nnz entries, sorted within each row */
+    const void    *val;      /* nnz values of type `dtype` */
+    int32_t        dtype;    /* ZOLO_R64, ZOLO_C128 or ZOLO_C64 */
+    int32_t        mem;      /* ZOLO_HOST (0) or ZOLO_DEVICE: where the three arrays live */
 } zolo_csr;
 
 /* Filter specification: the eigengaps (a-, a+) around a and (b-, b+) around b
  * (Section 1.2; the gap-estimation step of Algorithm 2).  a_minus may be -INFINITY (the
  * lowest slice, as in Section 3.1).  r1 / r2 are the inner (factored) and outer
- * (GMRES) Zolotarev orders; if either is <= 0 the smallest r = r1 = r2 with
- * delta0 <= eps is chosen (Remark after Algorithm 2).                       */
+ * (GMRES) Zolotarev orders.  Orders chosen from eps (Remark after Algorithm 2: the error
+ * of R_ab is (1 - S(l1; l1)) / 2, a function of (r1, r2) alone, evaluated without any
+ * matrix): r1, r2 <= 0 -> the smallest r = r1 = r2 with delta0 <= eps; r1 > 0, r2 <= 0
+ * -> the smallest r2 for that r1 (the factorisation count is fixed, e.g. by memory);
+ * r1 <= 0, r2 > 0 -> the smallest r1 for that r2.                               */
 typedef struct {
     double  a_minus, a_plus, b_minus, b_plus;
     int32_t r1, r2;
@@ -102,6 +118,9 @@ typedef struct {
     double  M;                          /* M of the outer Z_2r2(.; l2)                 */
     double  a[ZOLO_MAX_R];              /* outer weights a_j (Cor. 1)                  */
     double  c[ZOLO_MAX_R];              /* outer c_{2j-1}: shifts are +-i sqrt(c)      */
+    double  gap[4];                     /* the eigengaps a-, a+, b-, b+ of the spec      */
+    int32_t kind;                       /* ZOLO_FILTER_ZOLO, ZOLO_FILTER_CITZ or _CIGQ   */
+    int32_t npoles;                     /* contour filters: quadrature points (2 r1)     */
 } zolo_filter_info;
 
 /* Options.  zolo_opts_default() fills the documented defaults. */
@@ -131,6 +150,19 @@ typedef struct {
     uint64_t seed;         /* starting block: SplitMix64-seeded normal entries     */
     int32_t  verbose;      /* 0 silent, 1 stages to stderr                         */
     int32_t  tensor_core;  /* ZOLO_PREC_MIXED GEMMs: ZOLO_TC_AUTO (default), _OFF, _ALWAYS */
+    int32_t  gmres_chunk;  /* GMRES columns per chunk at most (the columns are independent
+                              problems); <= 0: as many as fit a Krylov basis of
+                              min(100 GiB, 60% of free device memory)           */
+    int32_t  split_k_min;  /* block solves: a launch with fewer than ~4 waves of tiles splits
+                              the inner extent of its accumulating products over several
+                              CTAs when that extent is >= split_k_min (default 512) */
+    int32_t  real_block;   /* real pencils: 1 (default) keeps real blocks real -- a real
+                              starting block, one solve per pole (K_j^-H B x = conj(K_j^-1 B x)
+                              for real A, B, x: eq. solve), real Krylov vectors; 0 runs the
+                              complex arithmetic of a Hermitian pencil              */
+    int32_t  lock;         /* Algorithm 1: 1 (default) locks converged Ritz pairs in (a, b)
+                              (they are no longer filtered; each Rayleigh-Ritz step still
+                              includes them), 0 filters the whole block every iteration */
 } zolo_opts;
 
 /* Counters and timings filled by zolo_apply / zolo_eigs (n_solv as Section 3 counts it). */
@@ -176,8 +208,22 @@ int         zolo_version(void);                 /* 100 * major + minor */
  * EINVAL unless a- < a+ < b- < b+ (a- may be -inf), 1 <= r <= ZOLO_MAX_R.       */
 int  zolo_filter_build(const zolo_filter_spec *spec, zolo_filter *out);
 int  zolo_filter_get_info(zolo_filter f, zolo_filter_info *out);
-/* R_ab(x[i]) for n real points, host arrays. */
+/* R_ab(x[i]) for n real points, host arrays (any filter kind). */
 int  zolo_filter_eval(zolo_filter f, int64_t n, const double *x, double *out);
+/* The table of the Remark after Algorithm 2: delta0[(r1 - 1) rmax + (r2 - 1)] = error
+ * (1 - S(l1; l1)) / 2 of R_ab with orders (r1, r2), 1 <= r1, r2 <= rmax <= ZOLO_MAX_R, for
+ * the gaps of `spec` (its r1, r2, eps are ignored).  Host only.                       */
+int  zolo_filter_table(const zolo_filter_spec *spec, int32_t rmax, double *delta0);
+/* Contour-integral filters (Section 1.1, eq. contourintegral): the circle with centre
+ * (a + b)/2 through a and b, discretised with npoles (even, 2..2 ZOLO_MAX_R) quadrature
+ * points -- kind ZOLO_FILTER_CITZ: trapezoidal rule at angles 2 pi (j - 1/2) / npoles;
+ * ZOLO_FILTER_CIGQ: npoles/2 Gauss-Legendre points on each half circle.  The points come in
+ * conjugate pairs, so the filter is applied like the inner function of Algorithm 2: r1 =
+ * npoles/2 factored poles sigma_j (upper half plane) with weights w_j and their conjugates
+ * through K_j^-H (eq. solve), const = 0 and no outer GMRES (r2 = 0).  R(x) = sum over all
+ * points of c_j / (z_j - x), c_j the quadrature weight times (z_j - centre) / npoles
+ * (trapezoid) or the Gauss-Legendre weight times (z_j - centre) / 4.                    */
+int  zolo_filter_build_contour(int32_t kind, double a, double b, int32_t npoles, zolo_filter *out);
 void zolo_filter_destroy(zolo_filter f);
 
 /* ---- ordering and symbolic analysis (host only, once per pattern) ------- */
@@ -221,18 +267,19 @@ int  zolo_factor_get_stats(zolo_factor_h h, zolo_stats *out);
  * overlap.  0 <= pole < r1.                                                      */
 int  zolo_solve(zolo_factor_h h, int32_t pole, int32_t herm, int64_t k, const void *Bk,
                 int64_t ldb, void *X, int64_t ldx, void *stream);
-/* zolo_solve without device allocation (the paper has no counterpart: this serves callers
- * that must not allocate on the calls they repeat -- work recorded into a CUDA graph by
- * stream capture, where cudaMalloc is not allowed, allocation-free real-time loops, or hosts
- * whose device memory pool belongs to someone else).  Same result as zolo_solve for a
- * complex128 (ZOLO_PREC_FP64) handle; the front workspaces come from one fixed device array
- * of 32 MiB that every GPU loading the library holds until exit, so
- * (rows of all fronts + n) * k * 16 bytes must fit in it (EINVAL otherwise, with the sizes).
- * Set-up: create the handle and call zolo_solve once with the same k (both allocate); the
- * first zolo_solve_noalloc call on a device looks up the array's device address, so make
- * that first call before any stream capture.  All calls share the array and it keeps the
- * last call's contents (each call clears what it needs): calls that overlap on the GPU
- * race.  EINVAL for MIXED handles or a k without a schedule.  Synchronises `stream`.     */
+/* zolo_solve without device allocation.  The paper has no counterpart: this serves callers
+ * that cannot call cudaMalloc on the calls they repeat -- hosts whose device memory belongs to
+ * another component (a framework's caching allocator, a pool that must own every byte) and
+ * allocation-free real-time loops, where an allocation could block or fail part-way.  Same
+ * result as zolo_solve for a complex128 (ZOLO_PREC_FP64) handle; the front workspaces come
+ * from one fixed device array of 32 MiB that every GPU loading the library holds until exit,
+ * so (rows of all fronts + n) * k * 16 bytes must fit in it (EINVAL otherwise, with the
+ * sizes).  Set-up: create the handle and call zolo_solve once with the same k (both
+ * allocate); the first zolo_solve_noalloc call on a device looks up the array's device
+ * address.  The current device must be the handle's (EINVAL otherwise).  All calls share
+ * the array and it keeps the last call's contents (each call clears what it needs): calls
+ * that overlap on the GPU race.  EINVAL for MIXED handles or a k without a schedule.
+ * Asynchronous: returns once the work is queued on `stream`; synchronise it before reading X. */
 int  zolo_solve_noalloc(zolo_factor_h h, int32_t pole, int32_t herm, int64_t k, const void *Bk,
                         int64_t ldb, void *X, int64_t ldx, void *stream);
 /* Y := A X (which = 0) or B X (which = 1), device blocks (SpMM with the uploaded CSR). */
@@ -248,15 +295,14 @@ int  zolo_apply(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y,
 
 /* ---- the eigensolver (Algorithm 1 with Algorithm 2 as the filter) ------- */
 /* Eigenpairs of (A, B) in (a, b) for an existing factor handle (its filter fixes the
- * gaps).  When n_iter_max > 1 the first filter application, which starts from a random
- * block, runs GMRES to max(gmres_tol, 1e-6) only: its output is filtered again by the
- * next iteration; later applications use gmres_tol.  Results: see below.
- *
- * gaps).  k0: subspace dimension (n_est estimate -> opts).  Results: evals[cap]
- * ascending (host), evecs n x cap device block (row-major, ld = ldv, B-orthonormal),
- * resid[cap] host residuals ||A x - lam B x||/(||A||_inf ||x||).  X0 (device, n x k0,
- * ld = k0) is the starting block, or NULL for the seeded normal block.  On ENOCONV the
- * best pairs found are still returned.                                          */
+ * gaps); Algorithm 1 with Algorithm 2 as the filter.  k0: subspace dimension.  When
+ * n_iter_max > 1 the first filter application, which starts from a random block, runs
+ * GMRES to max(gmres_tol, 1e-6) only: its output is filtered again by the next iteration;
+ * later applications use gmres_tol.  Results: evals[cap] ascending (host), evecs n x cap
+ * device block (row-major, ld = ldv, B-orthonormal), resid[cap] host residuals
+ * ||A x - lam B x|| / (||A||_inf ||x||).  X0 (device, n x k0, ld = k0) is the starting
+ * block, or NULL for the seeded normal block.  On ENOCONV the best pairs found are still
+ * returned.                                                                     */
 int  zolo_eigs_factored(zolo_factor_h h, double a, double b, int64_t k0, const void *X0,
                         double *evals, void *evecs, int64_t ldv, int64_t cap, int64_t *n_found,
                         double *resid, zolo_stats *stats, void *stream);

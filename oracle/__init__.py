@@ -5,7 +5,7 @@ only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl
 reference`` legs of ``bench.py`` use it.  It shares no code with
 ``paper_1701_08935_gb300`` (no kernels, helpers, tables or constant generators);
 the only shared module is the seeded input generator
-``paper_1701_08935_gb300.synth``, which holds no arithmetic of the method.
+``synth`` (a top-level module outside the package), which holds no arithmetic of the method.
 
 Every function is a plain, slow, readable restatement of the paper's
 definitions in float64 / complex128, written with numpy (library primitives

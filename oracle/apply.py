@@ -115,3 +115,10 @@ def apply_hybrid(A, B, X, flt, tol=1e-12, m_max=100, G=None, return_info=False):
     if return_info:
         return Y, {"m": m, "H": H[:m + 1, :m, :], "beta": beta, "V": V[:m + 1]}
     return Y
+
+
+def apply_contour(A, B, X, flt):
+    """R(B^-1 A) X for a contour-integral filter: every quadrature point is a factored pole,
+    R(B^-1 A) X = sum_j c_j (z_j - B^-1 A)^-1 X = sum_j w_j (A - z_j B)^-1 B X over all points
+    (w_j = -c_j), written through the upper-half poles and K^-H for their conjugates."""
+    return InnerOperator(A, B, flt)(np.asarray(X, dtype=np.complex128))

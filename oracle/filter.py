@@ -223,3 +223,64 @@ def composite_poles(flt):
     big = Zolotarev(2 * flt.r1 * flt.r2, flt.ell1)
     s, w, const = prop2_poles(big, flt.alpha, flt.beta, flt.gamma, rescale=1.0)
     return s, 0.5 * w, 0.5 + 0.5 * const, big
+
+
+# ----------------------------------------------------------------------------- order table
+def delta0_table(a_minus, a_plus, b_minus, b_plus, rmax):
+    """The table the Remark after Algorithm 2 suggests: delta0 = (1 - S(l1; l1))/2 for every
+    (r1, r2) in [1, rmax]^2, table[r1 - 1, r2 - 1]."""
+    t = np.zeros((rmax, rmax))
+    for r1 in range(1, rmax + 1):
+        for r2 in range(1, rmax + 1):
+            t[r1 - 1, r2 - 1] = ZoloFilter(a_minus, a_plus, b_minus, b_plus, r1, r2).delta0
+    return t
+
+
+# ----------------------------------------------------------------------------- contour filters
+class ContourFilter:
+    """Rational filters from discretising the contour integral (Section 1.1, eq.
+    contourintegral): (1/(2 pi i)) closed integral of dz / (z - x) over the circle with
+    centre c = (a+b)/2 and radius rho = (b-a)/2, which is 1 for x inside and 0 outside.
+    With z = c + rho e^{i theta}, dz = i rho e^{i theta} d theta, so a rule with nodes
+    theta_j and weights h_j (in theta) gives R(x) = sum_j c_j / (z_j - x),
+    c_j = h_j rho e^{i theta_j} / (2 pi).
+
+      kind "CITZ": trapezoidal rule, npoles nodes theta_j = 2 pi (j - 1/2)/npoles, h_j = 2 pi / npoles.
+      kind "CIGQ": Gauss-Legendre with npoles/2 nodes on each half circle; on the upper one
+                   theta = (pi/2)(1 + t), h = (pi/2) omega for the Legendre nodes t, weights omega;
+                   the lower half circle is its mirror image (theta -> -theta).
+
+    For the apply, the upper-half nodes are the factored poles sigma_hat with weights
+    w_hat = -c_j (c_j / (z_j - x) = w_j / (x - z_j)); each lower node is a conjugate pole
+    whose weight is the conjugate, so R(x) = sum_j 2 Re(w_j / (x - sigma_j)), const 0.
+    """
+
+    def __init__(self, kind, a, b, npoles):
+        if npoles < 2 or npoles % 2:
+            raise ValueError("npoles must be even")
+        self.kind, self.a, self.b, self.npoles = kind, float(a), float(b), int(npoles)
+        self.center, self.rho = 0.5 * (self.a + self.b), 0.5 * (self.b - self.a)
+        if kind == "CITZ":
+            theta = 2.0 * np.pi * (np.arange(1, npoles + 1) - 0.5) / npoles
+            h = np.full(npoles, 2.0 * np.pi / npoles)
+        elif kind == "CIGQ":
+            t, om = np.polynomial.legendre.leggauss(npoles // 2)
+            up = 0.5 * np.pi * (1.0 + t)
+            theta = np.concatenate([up, -up])
+            h = np.concatenate([0.5 * np.pi * om, 0.5 * np.pi * om])
+        else:
+            raise ValueError(kind)
+        self.z = self.center + self.rho * np.exp(1j * theta)
+        self.c = h * self.rho * np.exp(1j * theta) / (2.0 * np.pi)
+        upper = self.z.imag > 0
+        self.sigma_hat = self.z[upper]
+        self.w_hat = -self.c[upper]
+        self.const_hat = 0.0
+        self.r1 = len(self.sigma_hat)
+
+    def __call__(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        out = np.zeros(x.shape, dtype=np.complex128)
+        for zj, cj in zip(self.z, self.c):
+            out += cj / (zj - x)
+        return out.real

@@ -20,7 +20,9 @@ if not os.path.exists(_LIBPATH):
 lib = C.CDLL(_LIBPATH)
 
 OK, EINVAL, ENOTHERM, ENOMEM, ESINGULAR, ENOCONV, ETIMEOUT, ECUDA, EGAP = range(9)
-R64, C128 = 1, 2
+FILTER_ZOLO, FILTER_CITZ, FILTER_CIGQ = 0, 1, 2
+R64, C128, C64 = 1, 2, 3
+HOST, DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 TC_AUTO, TC_OFF, TC_ALWAYS = 0, 1, 2
 MAX_R = 16
@@ -37,7 +39,7 @@ class ZoloError(RuntimeError):
 
 class Csr(C.Structure):
     _fields_ = [("n", _i64), ("nnz", _i64), ("row_ptr", _vp), ("col_idx", _vp), ("val", _vp),
-                ("dtype", _i32), ("reserved", _i32)]
+                ("dtype", _i32), ("mem", _i32)]
 
 
 class FilterSpec(C.Structure):
@@ -50,14 +52,15 @@ class FilterInfo(C.Structure):
                 ("delta1", _dbl), ("delta0", _dbl), ("r1", _i32), ("r2", _i32), ("M_hat", _dbl),
                 ("const_hat", _dbl), ("a_hat", _dbl * MAX_R), ("c_hat", _dbl * MAX_R),
                 ("sigma_hat", _dbl * (2 * MAX_R)), ("w_hat", _dbl * (2 * MAX_R)), ("M", _dbl),
-                ("a", _dbl * MAX_R), ("c", _dbl * MAX_R)]
+                ("a", _dbl * MAX_R), ("c", _dbl * MAX_R), ("gap", _dbl * 4), ("kind", _i32), ("npoles", _i32)]
 
 
 class Opts(C.Structure):
     _fields_ = [("grid", _i32 * 3), ("leaf_max", _i32), ("precision", _i32), ("gmres_m_max", _i32),
                 ("gmres_tol", _dbl), ("refine_max", _i32), ("refine_tol", _dbl), ("n_iter_max", _i32),
                 ("tol", _dbl), ("drop_tol", _dbl), ("k", _i32), ("r1", _i32), ("r2", _i32),
-                ("gap_rel", _dbl), ("seed", _u64), ("verbose", _i32), ("tensor_core", _i32)]
+                ("gap_rel", _dbl), ("seed", _u64), ("verbose", _i32), ("tensor_core", _i32),
+                ("gmres_chunk", _i32), ("split_k_min", _i32), ("real_block", _i32), ("lock", _i32)]
 
 
 class Stats(C.Structure):
@@ -95,6 +98,8 @@ _sig("zolo_filter_build", C.c_int, [_P(FilterSpec), _P(_vp)])
 _sig("zolo_filter_get_info", C.c_int, [_vp, _P(FilterInfo)])
 _sig("zolo_filter_eval", C.c_int, [_vp, _i64, _vp, _vp])
 _sig("zolo_filter_destroy", None, [_vp])
+_sig("zolo_filter_table", C.c_int, [_P(FilterSpec), _i32, _vp])
+_sig("zolo_filter_build_contour", C.c_int, [_i32, _dbl, _dbl, _i32, _P(_vp)])
 _sig("zolo_analyze", C.c_int, [_P(Csr), _P(Csr), _P(Opts), _P(_vp)])
 _sig("zolo_symbolic_get_info", C.c_int, [_vp, _P(SymInfo)])
 _sig("zolo_symbolic_export", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp])
@@ -120,6 +125,7 @@ _sig("zolo_eigs_slices", C.c_int, [_P(Csr), _P(Csr), C.c_int32, _vp, _P(Opts), _
                                    _vp, _P(Stats), _vp])
 
 EXPORTED = ["zolo_opts_default", "zolo_strerror", "zolo_last_error", "zolo_version", "zolo_filter_build",
+            "zolo_filter_table", "zolo_filter_build_contour",
             "zolo_filter_get_info", "zolo_filter_eval", "zolo_filter_destroy", "zolo_analyze",
             "zolo_symbolic_get_info", "zolo_symbolic_export", "zolo_symbolic_destroy", "zolo_factor",
             "zolo_refactor", "zolo_inertia", "zolo_solve_noalloc", "zolo_profile_begin", "zolo_profile_end",
@@ -168,6 +174,9 @@ class Filter:
         spec = FilterSpec(a_minus, a_plus, b_minus, b_plus, r1, r2, eps)
         h = _vp()
         _check(lib.zolo_filter_build(C.byref(spec), C.byref(h)), "zolo_filter_build")
+        self._init_from(h)
+
+    def _init_from(self, h):
         self.h = h
         inf = FilterInfo()
         _check(lib.zolo_filter_get_info(h, C.byref(inf)), "zolo_filter_get_info")
@@ -191,6 +200,25 @@ class Filter:
         if getattr(self, "h", None):
             lib.zolo_filter_destroy(self.h)
             self.h = None
+
+
+def filter_table(a_minus, a_plus, b_minus, b_plus, rmax):
+    """delta0 of R_ab for every order pair: table[r1 - 1, r2 - 1] (Remark after Algorithm 2)."""
+    spec = FilterSpec(a_minus, a_plus, b_minus, b_plus, 0, 0, 0.0)
+    out = np.zeros(rmax * rmax)
+    _check(lib.zolo_filter_table(C.byref(spec), int(rmax), out.ctypes.data), "zolo_filter_table")
+    return out.reshape(rmax, rmax)
+
+
+class ContourFilter(Filter):
+    """Contour-integral filter (eq. contourintegral) on the circle through a and b:
+    kind FILTER_CITZ (trapezoidal rule) or FILTER_CIGQ (Gauss-Legendre), npoles points."""
+
+    def __init__(self, kind, a, b, npoles):
+        h = _vp()
+        _check(lib.zolo_filter_build_contour(int(kind), float(a), float(b), int(npoles), C.byref(h)),
+               "zolo_filter_build_contour")
+        self._init_from(h)
 
 
 class Symbolic:
@@ -285,11 +313,25 @@ def _stream(stream):
     return _vp(int(stream))
 
 
-def _blk(t, name):
+def check_block(shape, name, n, k=None):
+    """Row and column counts of a block passed to the C ABI, which gets raw pointers and
+    cannot check sizes: a block with fewer rows or columns than the call reads or writes
+    is refused here, before any launch."""
+    if len(shape) != 2 or shape[1] < 1:
+        raise ValueError(f"{name}: need a non-empty 2-D block, got shape {tuple(shape)}")
+    if shape[0] != n:
+        raise ValueError(f"{name}: has {shape[0]} rows, the pencil has n = {n}")
+    if k is not None and shape[1] != k:
+        raise ValueError(f"{name}: has {shape[1]} columns, expected {k}")
+
+
+def _blk(t, name, n, k=None):
+    """Pointer, width and row stride of an (n, k) CUDA complex128 block."""
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.dim() == 2
             and t.stride(1) == 1):
         raise ValueError(f"{name}: need a CUDA complex128 tensor (n, k) with unit column stride")
+    check_block(tuple(t.shape), name, n, k)
     return _vp(t.data_ptr()), t.shape[1], t.stride(0)
 
 
@@ -316,42 +358,42 @@ class Factor:
 
     def solve(self, pole, B, herm=False, out=None, stream=None):
         import torch
-        pb, k, ldb = _blk(B, "B")
+        pb, k, ldb = _blk(B, "B", self.n)
         out = out if out is not None else torch.empty_like(B)
-        px, _, ldx = _blk(out, "out")
+        px, _, ldx = _blk(out, "out", self.n, k)
         _check(lib.zolo_solve(self.h, pole, 1 if herm else 0, k, pb, ldb, px, ldx, _stream(stream)), "zolo_solve")
         return out
 
     def solve_noalloc(self, pole, B, out, herm=False, stream=None):
         """zolo_solve through the fixed no-allocation workspace (see include/zolo.h)."""
-        pb, k, ldb = _blk(B, "B")
-        px, _, ldx = _blk(out, "out")
+        pb, k, ldb = _blk(B, "B", self.n)
+        px, _, ldx = _blk(out, "out", self.n, k)
         _check(lib.zolo_solve_noalloc(self.h, pole, 1 if herm else 0, k, pb, ldb, px, ldx, _stream(stream)),
                "zolo_solve_noalloc")
         return out
 
     def matmul(self, which, X, out=None, stream=None):
         import torch
-        px, k, ldx = _blk(X, "X")
+        px, k, ldx = _blk(X, "X", self.n)
         out = out if out is not None else torch.empty_like(X)
-        py, _, ldy = _blk(out, "out")
+        py, _, ldy = _blk(out, "out", self.n, k)
         _check(lib.zolo_matmul(self.h, 0 if which in ("A", 0) else 1, k, px, ldx, py, ldy, _stream(stream)),
                "zolo_matmul")
         return out
 
     def apply_inner(self, X, out=None, stream=None):
         import torch
-        px, k, ldx = _blk(X, "X")
+        px, k, ldx = _blk(X, "X", self.n)
         out = out if out is not None else torch.empty_like(X)
-        py, _, ldy = _blk(out, "out")
+        py, _, ldy = _blk(out, "out", self.n, k)
         _check(lib.zolo_apply_inner(self.h, k, px, ldx, py, ldy, _stream(stream)), "zolo_apply_inner")
         return out
 
     def apply(self, X, out=None, stream=None):
         import torch
-        px, k, ldx = _blk(X, "X")
+        px, k, ldx = _blk(X, "X", self.n)
         out = out if out is not None else torch.empty_like(X)
-        py, _, ldy = _blk(out, "out")
+        py, _, ldy = _blk(out, "out", self.n, k)
         st = Stats()
         _check(lib.zolo_apply(self.h, k, px, ldx, py, ldy, C.byref(st), _stream(stream)), "zolo_apply")
         return out, st.as_dict()
@@ -366,7 +408,7 @@ class Factor:
         st = Stats()
         x0 = _vp(X0.data_ptr()) if X0 is not None else None
         if X0 is not None:
-            _blk(X0, "X0")
+            _blk(X0, "X0", self.n, k0)
         rc = lib.zolo_eigs_factored(self.h, a, b, k0, x0, evals.ctypes.data, _vp(V.data_ptr()), cap, cap,
                                     C.byref(nf), resid.ctypes.data, C.byref(st), _stream(stream))
         if rc not in (OK, ENOCONV):

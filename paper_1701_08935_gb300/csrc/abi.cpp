@@ -34,6 +34,10 @@ void zolo_opts_default(zolo_opts *o) {
     o->r2 = 2;
     o->gap_rel = 1e-2;
     o->seed = 0x5eed;
+    o->gmres_chunk = 0;
+    o->split_k_min = 512;
+    o->real_block = 1;
+    o->lock = 1;
 }
 
 const char *zolo_strerror(int s) {

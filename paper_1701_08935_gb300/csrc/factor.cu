@@ -89,6 +89,8 @@ thread_local bool g_plan_c64 = false;
 thread_local int g_plan_tc = ZOLO_TC_AUTO;
 // Tile -> job map of the launches being planned (appended by add_gemm when set).
 thread_local std::vector<int32_t> *g_plan_tmap = nullptr;
+// Smallest inner extent of an accumulating product that add_gemm may split (zolo_opts.split_k_min).
+thread_local int g_plan_split_min = 512;
 // Complex64 launches whose jobs average at least this many rows go to the tensor cores.
 constexpr double TC_MIN_ROWS = 128.0;
 
@@ -97,7 +99,7 @@ constexpr double TC_MIN_ROWS = 128.0;
 // >= TC_MIN_ROWS rows (every launch with ZOLO_TC_ALWAYS, none with ZOLO_TC_OFF); otherwise
 // FP32-FMA tiles of 128 x 64 when they average >= 256 rows, 32 x 128 when <= 40, else
 // 64 x 64.  Complex128 launches take 64 x 64.  With allow_split, a launch with fewer than ~4 waves
-// of tiles splits the kk extent of its accumulating jobs (GJ_SUB / GJ_ACC, kk >= 512) over
+// of tiles splits the kk extent of its accumulating jobs (GJ_SUB / GJ_ACC, kk >= g_plan_split_min) over
 // several CTAs (atomic adds).
 Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool allow_split = false) {
     Launch L;
@@ -122,8 +124,11 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
         L.bn = 128;
         L.tc = true;
     }
-    auto splittable = [](const GJob &j) { return (j.flags & (GJ_SUB | GJ_ACC)) && j.k >= 512; };
-    auto split_of = [&](const GJob &j, int f) { return splittable(j) ? std::max(1, std::min({f, j.k / 256, 16})) : 1; };
+    const int kmin = std::max(16, g_plan_split_min);
+    auto splittable = [&](const GJob &j) { return (j.flags & (GJ_SUB | GJ_ACC)) && j.k >= kmin; };
+    auto split_of = [&](const GJob &j, int f) {
+        return splittable(j) ? std::max(1, std::min({f, j.k / (kmin / 2), 16})) : 1;
+    };
     auto tiles_of = [&](const GJob &j) { return ((j.m + L.bm - 1) / L.bm) * ((j.n + L.bn - 1) / L.bn); };
     int base = 0;
     for (const GJob &j : jobs)
@@ -652,6 +657,7 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
     const zolo_symbolic_s &S = h->sym;
     g_plan_c64 = (h->prec == ZOLO_PREC_MIXED);
     g_plan_tc = h->opts.tensor_core;
+    g_plan_split_min = h->opts.split_k_min > 0 ? h->opts.split_k_min : 512;
     std::vector<int32_t> stm;
     g_plan_tmap = &stm;
     struct ClearMap {
@@ -883,6 +889,47 @@ int ensure_scratch(zolo_factor_s *h, int64_t k, int blocks, c128 **out) {
     return ZOLO_OK;
 }
 
+int ensure_colpart(zolo_factor_s *h, int64_t k, double **out) {
+    const size_t need = (size_t)COLNORM_PARTS * std::max<int64_t>(k, 1) * sizeof(double);
+    if (h->colpart.bytes < need) {
+        dev_release(h, h->colpart);
+        void *p = nullptr;
+        int rc = dev_alloc(h, need, &p);
+        if (rc) return rc;
+        h->colpart = Buf{p, need};
+    }
+    *out = (double *)h->colpart.p;
+    return ZOLO_OK;
+}
+
+int colnorm2(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, double *out, cudaStream_t st, bool imag_only) {
+    double *part = nullptr;
+    int rc = ensure_colpart(h, k, &part);
+    if (rc) return rc;
+    launch_colnorm2(h->n, k, X, ldx, out, part, st, imag_only);
+    return ZOLO_OK;
+}
+
+int block_is_real(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, cudaStream_t st, bool *real) {
+    *real = false;
+    if (h->norms_k < k) {
+        if (h->d_norms) dev_free(h, h->d_norms);
+        int rc = dev_alloc(h, 2 * MAX_INST * k * sizeof(double), (void **)&h->d_norms);
+        if (rc) return rc;
+        h->norms_k = k;
+    }
+    int rc = colnorm2(h, k, X, ldx, h->d_norms, st, true);
+    if (rc) return rc;
+    std::vector<double> im(k);
+    rc = cuda_check(cudaMemcpyAsync(im.data(), h->d_norms, k * sizeof(double), cudaMemcpyDeviceToHost, st), "imag");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "imag");
+    if (rc) return rc;
+    bool r = true;
+    for (double v : im) r = r && (v == 0.0);
+    *real = r;
+    return ZOLO_OK;
+}
+
 int solve_refined(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int64_t k, const c128 *const *Xin,
                   int64_t ldin, c128 *const *Xout, int64_t ldout, cudaStream_t st, int *n_refine) {
     if (n_refine) *n_refine = 0;
@@ -914,7 +961,10 @@ int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, i
     }
     c128 *R = (c128 *)h->rscratch.p, *DX = R + ninst * blk;
     std::vector<double> hb(ninst * k), hr(ninst * k);
-    for (int z = 0; z < ninst; ++z) launch_colnorm2(h->n, k, Xin[z], ldin, h->d_norms + z * k, st);
+    for (int z = 0; z < ninst; ++z) {
+        int rc = colnorm2(h, k, Xin[z], ldin, h->d_norms + z * k, st);
+        if (rc) return rc;
+    }
     int rc = cuda_check(cudaMemcpyAsync(hb.data(), h->d_norms, ninst * k * sizeof(double), cudaMemcpyDeviceToHost, st),
                         "norms");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "norms");
@@ -960,7 +1010,8 @@ int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, i
         } else {
             launch_refine_resid(h->A, h->B, ra, st);
         }
-        for (int z = 0; z < ninst; ++z) launch_colnorm2(h->n, k, R + z * blk, k, h->d_norms + z * k, st);
+        for (int z = 0; z < ninst && !rc; ++z) rc = colnorm2(h, k, R + z * blk, k, h->d_norms + z * k, st);
+        if (rc) return rc;
         rc = cuda_check(cudaMemcpyAsync(hr.data(), h->d_norms, ninst * k * sizeof(double), cudaMemcpyDeviceToHost, st),
                         "norms");
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "norms");
@@ -1007,8 +1058,12 @@ int refine_loop(zolo_factor_s *h, int ninst, const int *pole, const int *herm, i
 int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st,
                 const float2 *Xs) {
     // GX = const_hat X + sum_j ( w_hat_j K_j^-1 B X + conj(w_hat_j) K_j^-H B X )   (eq. solve)
+    // With real A, B and X (h->realx), K_j^-H B X = conj(K_j^-1 B X), so
+    // GX = const_hat X + 2 Re sum_j w_hat_j K_j^-1 B X: one solve per pole.
     const int r1 = h->r1;
-    const int nblk = 1 + 2 * r1;
+    const bool rx = h->realx;
+    const int nsol = rx ? r1 : 2 * r1;                  // solve instances
+    const int nblk = 1 + nsol;
     c128 *scr = nullptr;
     int rc = ensure_scratch(h, k, nblk, &scr);
     if (rc) return rc;
@@ -1017,15 +1072,15 @@ int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
         launch_spmm_df(h->B, k, Xs, BX, st);
     else
         launch_spmm(h->B, k, X, ldx, BX, k, c128{1.0, 0.0}, false, st);
-    for (int p0 = 0; p0 < 2 * r1; p0 += MAX_INST) {
-        const int ni = std::min(MAX_INST, 2 * r1 - p0);
+    for (int p0 = 0; p0 < nsol; p0 += MAX_INST) {
+        const int ni = std::min(MAX_INST, nsol - p0);
         int pole[MAX_INST], herm[MAX_INST];
         const c128 *in[MAX_INST];
         c128 *out[MAX_INST];
         for (int z = 0; z < ni; ++z) {
             const int q = p0 + z;
-            pole[z] = q / 2;
-            herm[z] = q % 2;
+            pole[z] = rx ? q : q / 2;
+            herm[z] = rx ? 0 : q % 2;
             in[z] = BX;
             out[z] = scr + (size_t)(1 + q) * h->n * k;
         }
@@ -1040,25 +1095,25 @@ int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
     a.k = k;
     a.ldy = ldy;
     a.Y = Y;
+    a.real_out = rx ? 1 : 0;
     a.nterm = 0;
     a.coef[a.nterm] = c128{h->fi.const_hat, 0.0};
     a.X[a.nterm] = X;
     a.ldx[a.nterm++] = ldx;
     // the linear combination kernel takes at most LIN_MAX terms: accumulate in passes
-    for (int j = 0; j < r1; ++j) {
+    for (int q = 0; q < nsol; ++q) {
+        const int j = rx ? q : q / 2, hh = rx ? 0 : q % 2;
         const c128 w{h->fi.w_hat[2 * j], h->fi.w_hat[2 * j + 1]};
-        for (int hh = 0; hh < 2; ++hh) {
-            if (a.nterm == LIN_MAX) {
-                launch_lincomb(a, st);
-                a.nterm = 0;
-                a.coef[a.nterm] = c128{1.0, 0.0};
-                a.X[a.nterm] = Y;
-                a.ldx[a.nterm++] = ldy;
-            }
-            a.coef[a.nterm] = hh ? conj(w) : w;
-            a.X[a.nterm] = scr + (size_t)(1 + 2 * j + hh) * h->n * k;
-            a.ldx[a.nterm++] = k;
+        if (a.nterm == LIN_MAX) {
+            launch_lincomb(a, st);
+            a.nterm = 0;
+            a.coef[a.nterm] = c128{1.0, 0.0};
+            a.X[a.nterm] = Y;
+            a.ldx[a.nterm++] = ldy;
         }
+        a.coef[a.nterm] = rx ? c128{2.0 * w.re, 2.0 * w.im} : (hh ? conj(w) : w);
+        a.X[a.nterm] = scr + (size_t)(1 + q) * h->n * k;
+        a.ldx[a.nterm++] = k;
     }
     launch_lincomb(a, st);
     return cuda_check(cudaGetLastError(), "apply_inner");
@@ -1078,8 +1133,12 @@ namespace zolo {
 static int factor_create(const zolo_csr *A, const zolo_csr *B, const zolo_filter_info &fi, zolo_symbolic sym,
                          const zolo_opts *opts, cudaStream_t stream, bool count_neg, zolo_factor_s **out) {
     *out = nullptr;
+    CsrHost ha, hb;
+    int rc = csr_host_view(A, ha, &A);
+    if (!rc) rc = csr_host_view(B, hb, &B);
+    if (rc) return rc;
     bool ca, cb;
-    int rc = check_csr(A, "A", ca);
+    rc = check_csr(A, "A", ca);
     if (!rc) rc = check_csr(B, "B", cb);
     if (rc) return rc;
     if (A->n != B->n) return set_error(ZOLO_EINVAL, "A and B differ in size");
@@ -1150,6 +1209,10 @@ int zolo_inertia(const zolo_csr *A, const zolo_csr *B, zolo_symbolic sym, const 
                  const double *sigma, int64_t *count, void *stream) {
     clear_error();
     if (!sigma || !count || nshift < 1) return set_error(ZOLO_EINVAL, "bad argument");
+    CsrHost ha, hb;                                 // one host copy for every batch of shifts
+    int rc0 = csr_host_view(A, ha, &A);
+    if (!rc0) rc0 = csr_host_view(B, hb, &B);
+    if (rc0) return rc0;
     for (int i = 0; i < nshift; ++i)
         if (!std::isfinite(sigma[i])) return set_error(ZOLO_EINVAL, "non-finite shift");
     // Always complex128 fronts: the no-pivot LDL^H of an indefinite A - sigma B keeps the
@@ -1265,7 +1328,13 @@ int zolo_matmul(zolo_factor_h h, int32_t which, int64_t k, const void *X, int64_
 int zolo_apply_inner(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y, int64_t ldy, void *stream) {
     clear_error();
     if (!h || !X || !Y || k <= 0 || ldx < k || ldy < k) return set_error(ZOLO_EINVAL, "bad argument");
-    int rc = apply_inner(h, k, (const c128 *)X, ldx, (c128 *)Y, ldy, (cudaStream_t)stream);
+    bool rx = false;
+    int rc = ZOLO_OK;
+    if (pencil_is_real(h) && h->opts.real_block) rc = block_is_real(h, k, (const c128 *)X, ldx, (cudaStream_t)stream, &rx);
+    if (rc) return rc;
+    h->realx = rx;
+    rc = apply_inner(h, k, (const c128 *)X, ldx, (c128 *)Y, ldy, (cudaStream_t)stream);
+    h->realx = false;
     if (rc) return rc;
     return cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "apply_inner");
 }

@@ -103,6 +103,9 @@ struct zolo_factor_s {
     zolo::Buf scratch, rscratch;
     double *d_norms = nullptr;                     // column norms, 2 * MAX_INST * kmax
     int64_t norms_k = 0;
+    zolo::Buf colpart;                             // partial sums of the column-norm reduction
+    bool realx = false;                            // the current filter application works on real
+                                                   // blocks of a real pencil: one solve per pole
 
     zolo::KrylovWork *kw = nullptr;
     double gmres_tol_now = 0.0;                    // tolerance of the current filter application
@@ -136,4 +139,13 @@ int apply_inner(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
                 const float2 *Xs = nullptr);
 // scratch block of complex128 with at least `blocks` n x k blocks
 int ensure_scratch(zolo_factor_s *h, int64_t k, int blocks, c128 **out);
+// partial-sum buffer of launch_colnorm2 for blocks of up to k columns
+int ensure_colpart(zolo_factor_s *h, int64_t k, double **out);
+// sum of squared column norms of X (n x k) into out[0..k) on the device
+int colnorm2(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, double *out, cudaStream_t st,
+             bool imag_only = false);
+// true when the pencil's values are all real (A and B)
+inline bool pencil_is_real(const zolo_factor_s *h) { return h->A.vr && h->B.vr; }
+// whether every entry of the n x k device block X has a zero imaginary part (synchronises)
+int block_is_real(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, cudaStream_t st, bool *real);
 }  // namespace zolo

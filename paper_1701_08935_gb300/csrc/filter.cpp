@@ -113,6 +113,16 @@ int zolo_build(int r, double ell, Zolo &z) {
 }  // namespace zolo
 
 double zolo_filter_s::eval(double x) const {
+    if (kind != ZOLO_FILTER_ZOLO) {
+        // contour filters: sum over the conjugate point pairs of 2 Re(w_j / (x - sigma_j))
+        double v = 0.0;
+        for (int j = 0; j < info.r1; ++j) {
+            const zolo::cplx w(info.w_hat[2 * j], info.w_hat[2 * j + 1]);
+            const zolo::cplx sg(info.sigma_hat[2 * j], info.sigma_hat[2 * j + 1]);
+            v += 2.0 * (w / (x - sg)).real();
+        }
+        return v;
+    }
     // R_ab(x) = (Z_2r2(Zhat_2r1(T(x); l1); l2) + 1)/2;  T(beta) = inf maps to Zhat = 0
     double zi;
     if (x == beta) {
@@ -139,8 +149,7 @@ int zolo_filter_build(const zolo_filter_spec *spec, zolo_filter *out) {
         return set_error(ZOLO_EINVAL, "need a- < a+ < b- < b+");
     int r1 = spec->r1, r2 = spec->r2;
     const bool auto_r = (r1 <= 0 || r2 <= 0);
-    if (!auto_r && (r1 > ZOLO_MAX_R || r2 > ZOLO_MAX_R))
-        return set_error(ZOLO_EINVAL, "r1, r2 must be <= ZOLO_MAX_R");
+    if (r1 > ZOLO_MAX_R || r2 > ZOLO_MAX_R) return set_error(ZOLO_EINVAL, "r1, r2 must be <= ZOLO_MAX_R");
     if (auto_r && !(spec->eps > 0.0 && spec->eps < 0.5))
         return set_error(ZOLO_EINVAL, "automatic order needs 0 < eps < 0.5");
 
@@ -177,14 +186,18 @@ int zolo_filter_build(const zolo_filter_spec *spec, zolo_filter *out) {
     };
     int st = ZOLO_OK;
     if (auto_r) {
+        // Remark after Algorithm 2: the error (1 - S(l1; l1))/2 needs no matrix, so walk the
+        // free order(s) upwards until it is <= eps
+        const int fix1 = r1 > 0 ? r1 : 0, fix2 = r2 > 0 ? r2 : 0;
         int r = 1;
         for (; r <= ZOLO_MAX_R; ++r) {
-            st = build_pair(r, r);
+            st = build_pair(fix1 ? fix1 : r, fix2 ? fix2 : r);
             if (st) break;
             if (F->delta0 <= spec->eps) break;
         }
-        if (!st && r > ZOLO_MAX_R) st = set_error(ZOLO_EINVAL, "eps not reachable with r <= ZOLO_MAX_R");
-        r1 = r2 = r;
+        if (!st && r > ZOLO_MAX_R) st = set_error(ZOLO_EINVAL, "eps not reachable with orders <= ZOLO_MAX_R");
+        r1 = fix1 ? fix1 : r;
+        r2 = fix2 ? fix2 : r;
     } else {
         st = build_pair(r1, r2);
     }
@@ -225,6 +238,106 @@ int zolo_filter_build(const zolo_filter_spec *spec, zolo_filter *out) {
     for (int j = 0; j < r2; ++j) {
         I.a[j] = F->outer.a[j];
         I.c[j] = F->outer.c[2 * j];
+    }
+    I.gap[0] = am;
+    I.gap[1] = ap;
+    I.gap[2] = bm;
+    I.gap[3] = bp;
+    I.kind = ZOLO_FILTER_ZOLO;
+    *out = F;
+    return ZOLO_OK;
+}
+
+int zolo_filter_table(const zolo_filter_spec *spec, int32_t rmax, double *delta0) {
+    using namespace zolo;
+    clear_error();
+    if (!spec || !delta0 || rmax < 1 || rmax > ZOLO_MAX_R) return set_error(ZOLO_EINVAL, "bad argument");
+    for (int r1 = 1; r1 <= rmax; ++r1)
+        for (int r2 = 1; r2 <= rmax; ++r2) {
+            zolo_filter_spec s = *spec;
+            s.r1 = r1;
+            s.r2 = r2;
+            zolo_filter f = nullptr;
+            const int st = zolo_filter_build(&s, &f);
+            if (st) return st;
+            delta0[(r1 - 1) * rmax + (r2 - 1)] = f->delta0;
+            zolo_filter_destroy(f);
+        }
+    return ZOLO_OK;
+}
+
+int zolo_filter_build_contour(int32_t kind, double a, double b, int32_t npoles, zolo_filter *out) {
+    using namespace zolo;
+    clear_error();
+    if (!out) return set_error(ZOLO_EINVAL, "null argument");
+    *out = nullptr;
+    if (kind != ZOLO_FILTER_CITZ && kind != ZOLO_FILTER_CIGQ) return set_error(ZOLO_EINVAL, "unknown contour filter kind");
+    if (!(std::isfinite(a) && std::isfinite(b) && a < b)) return set_error(ZOLO_EINVAL, "need finite a < b");
+    if (npoles < 2 || npoles % 2 || npoles > 2 * ZOLO_MAX_R)
+        return set_error(ZOLO_EINVAL, "npoles must be even, 2 .. 2 ZOLO_MAX_R");
+    const int h = npoles / 2;                          // points in the upper half plane
+    const double c0 = 0.5 * (a + b), rho = 0.5 * (b - a);
+    std::vector<double> theta(h), wq(h);
+    if (kind == ZOLO_FILTER_CITZ) {
+        // trapezoidal rule in the angle: z_j = c0 + rho e^{i theta_j}, theta_j = 2 pi (j - 1/2)/npoles;
+        // the weight of (1/(2 pi i)) dz/(z - x) at z_j is rho e^{i theta_j} / npoles
+        for (int j = 0; j < h; ++j) {
+            theta[j] = 2.0 * M_PI * (j + 0.5) / npoles;
+            wq[j] = 1.0 / npoles;
+        }
+    } else {
+        // Gauss-Legendre on the upper half circle: theta = (pi/2)(1 + t), t the Legendre nodes of
+        // degree h on [-1, 1] (Newton on the three-term recurrence), dtheta = (pi/2) dt, so the
+        // weight at z_j is rho e^{i theta_j} omega_j / 4
+        for (int i = 0; i < h; ++i) {
+            double x = std::cos(M_PI * (i + 0.75) / (h + 0.5));
+            double dp = 1.0;
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = x;
+                for (int j = 2; j <= h; ++j) {
+                    const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                if (h == 1) { p1 = x; p0 = 1.0; }
+                dp = h * (x * p1 - p0) / (x * x - 1.0);
+                const double dx = p1 / dp;
+                x -= dx;
+                if (std::fabs(dx) <= 1e-16 * std::max(1.0, std::fabs(x))) break;
+            }
+            {   // derivative at the converged node
+                double p0 = 1.0, p1 = x;
+                for (int j = 2; j <= h; ++j) {
+                    const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                if (h == 1) { p1 = x; p0 = 1.0; }
+                dp = h * (x * p1 - p0) / (x * x - 1.0);
+            }
+            theta[i] = 0.5 * M_PI * (1.0 + x);
+            wq[i] = 2.0 / ((1.0 - x * x) * dp * dp) / 4.0;
+        }
+    }
+    auto *F = new zolo_filter_s();
+    std::memset(&F->spec, 0, sizeof(F->spec));
+    F->kind = kind;
+    zolo_filter_info &I = F->info;
+    std::memset(&I, 0, sizeof(I));
+    I.kind = kind;
+    I.npoles = npoles;
+    I.r1 = h;
+    I.r2 = 0;
+    I.gap[0] = I.gap[1] = a;
+    I.gap[2] = I.gap[3] = b;
+    for (int j = 0; j < h; ++j) {
+        const cplx e(std::cos(theta[j]), std::sin(theta[j]));
+        const cplx z = c0 + rho * e;
+        const cplx cj = rho * e * wq[j];               // R(x) = sum_j c_j / (z_j - x) + conjugates
+        I.sigma_hat[2 * j] = z.real();
+        I.sigma_hat[2 * j + 1] = z.imag();
+        I.w_hat[2 * j] = -cj.real();                   // w_j / (x - z_j) = c_j / (z_j - x)
+        I.w_hat[2 * j + 1] = -cj.imag();
     }
     *out = F;
     return ZOLO_OK;

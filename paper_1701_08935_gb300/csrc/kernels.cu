@@ -788,6 +788,7 @@ __global__ void k_lincomb(LinArgs a) {
     const int64_t i = idx / a.k, c = idx - i * a.k;
     c128 s = mk<double>(0, 0);
     for (int t = 0; t < a.nterm; ++t) fma_acc(s, a.coef[t], a.X[t][i * a.ldx[t] + c]);
+    if (a.real_out) s.im = 0.0;
     a.Y[i * a.ldy + c] = s;
 }
 
@@ -799,34 +800,35 @@ void launch_lincomb(const LinArgs &a, cudaStream_t st) {
 }
 
 // ============================================================== column norms
-// stage 1: CTA b sums rows b, b + G, b + 2G, ... into part[b * k + c];  stage 2 sums parts.
-constexpr int NORM_CTAS = 304;
+// stage 1: CTA b sums rows b, b + G, b + 2G, ... into part[b * k + c];  stage 2: one warp
+// per column adds the COLNORM_PARTS partial sums (fixed order: deterministic).
 __global__ void __launch_bounds__(256) k_colnorm_part(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx,
-                                                      double *__restrict__ part) {
+                                                      double *__restrict__ part, int imag_only) {
     for (int c = threadIdx.x; c < k; c += 256) {
         double s = 0.0;
-        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s += abs2(X[i * ldx + c]);
+        if (imag_only)
+            for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s = fma(X[i * ldx + c].im, X[i * ldx + c].im, s);
+        else
+            for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s += abs2(X[i * ldx + c]);
         part[(int64_t)blockIdx.x * k + c] = s;
     }
 }
-__global__ void k_colnorm_sum(int k, int parts, const double *__restrict__ part, double *__restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_colnorm_sum(int k, int parts, const double *__restrict__ part,
+                                                     double *__restrict__ out) {
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (c >= k) return;
     double s = 0.0;
-    for (int b = 0; b < parts; ++b) s += part[(int64_t)b * k + c];
-    out[c] = s;
+    for (int b = lane; b < parts; b += 32) s += part[(int64_t)b * k + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[c] = s;
 }
 
-void launch_colnorm2(int64_t n, int64_t k, const c128 *X, int64_t ldx, double *out, cudaStream_t st) {
-    static double *part = nullptr;
-    static int64_t cap = 0;
-    if (cap < NORM_CTAS * k) {
-        if (part) cudaFree(part);
-        cudaMalloc(&part, NORM_CTAS * k * sizeof(double));
-        cap = NORM_CTAS * k;
-    }
-    k_colnorm_part<<<NORM_CTAS, 256, 0, st>>>(n, (int)k, X, ldx, part);
-    k_colnorm_sum<<<(unsigned)((k + 255) / 256), 256, 0, st>>>((int)k, NORM_CTAS, part, out);
+void launch_colnorm2(int64_t n, int64_t k, const c128 *X, int64_t ldx, double *out, double *part, cudaStream_t st,
+                     bool imag_only) {
+    if (k <= 0) return;
+    k_colnorm_part<<<COLNORM_PARTS, 256, 0, st>>>(n, (int)k, X, ldx, part, imag_only ? 1 : 0);
+    k_colnorm_sum<<<(unsigned)((k + 7) / 8), 256, 0, st>>>((int)k, COLNORM_PARTS, part, out);
     g_counters.launches += 2;
 }
 

@@ -98,6 +98,7 @@ constexpr int LIN_MAX = 8;
 struct LinArgs {
     int64_t n, k, ldy;
     int nterm;
+    int real_out;                        // 1: keep the real part of the sum only
     c128 coef[LIN_MAX];
     const c128 *X[LIN_MAX];
     int64_t ldx[LIN_MAX];
@@ -139,7 +140,10 @@ template <class T> void launch_eye(const EyeArgs<T> &g, int ninst, cudaStream_t 
 void launch_spmm(const DevCSR &M, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, c128 s, bool acc,
                  cudaStream_t st);
 void launch_lincomb(const LinArgs &a, cudaStream_t st);
-// out[c] = sum_i |X[i, c]|^2 for an n x k block (deterministic two-stage reduction)
-void launch_colnorm2(int64_t n, int64_t k, const c128 *X, int64_t ldx, double *out, cudaStream_t st);
+// out[c] = sum_i |X[i, c]|^2 for an n x k block (imag_only: sum_i Im(X[i, c])^2), by a
+// deterministic two-stage reduction through `part` (COLNORM_PARTS * k doubles, device)
+constexpr int COLNORM_PARTS = 304;
+void launch_colnorm2(int64_t n, int64_t k, const c128 *X, int64_t ldx, double *out, double *part, cudaStream_t st,
+                     bool imag_only = false);
 
 }  // namespace zolo

@@ -236,8 +236,10 @@ __global__ void k_zeta(int k, int ns, int m, int mmax, const c128 *__restrict__ 
     zeta[(int64_t)j * k + c] = s;
 }
 // Y[i,c] = X[i,c]/2 + sum_{j<m} V_j[i,c] zeta[j][c]
+// (real_out: the real part only, for the real blocks of a real pencil, where the conjugate
+// shift pairs give conjugate z_s and a real sum up to rounding)
 __global__ void k_combine(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx, const float2 *const *__restrict__ V,
-                          int m, const c128 *__restrict__ zeta, c128 *__restrict__ Y, int64_t ldy) {
+                          int m, const c128 *__restrict__ zeta, c128 *__restrict__ Y, int64_t ldy, int real_out) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nk = n * k;
     if (idx >= nk) return;
@@ -249,6 +251,7 @@ __global__ void k_combine(int64_t n, int k, const c128 *__restrict__ X, int64_t 
         const c128 v = mk<double>(df_widen(hi.x) + df_widen(lo.x), df_widen(hi.y) + df_widen(lo.y));
         fma_acc(y, v, zeta[(int64_t)j * k + c]);
     }
+    if (real_out) y.im = 0.0;
     Y[i * ldy + c] = y;
 }
 
@@ -387,6 +390,14 @@ __global__ void k_resid_block(int64_t n, int m, const c128 *AQ, const c128 *BQ, 
     const int c = (int)(idx % m);
     R[idx] = AQ[idx] - lam[c] * BQ[idx];
 }
+// D[i, t] = S[i, t] for t < nc  (row-major blocks, ld ldd / lds)
+__global__ void k_copy_cols(int64_t n, int nc, const c128 *S, int64_t lds, c128 *D, int64_t ldd) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * nc) return;
+    const int64_t i = idx / nc;
+    const int t = (int)(idx - i * nc);
+    D[i * ldd + t] = S[i * lds + t];
+}
 // E[i, t] = Q[i, sel[t]]  (row-major blocks, ld lde / ldq)
 __global__ void k_select_cols(int64_t n, int nf, const c128 *Q, int64_t ldq, const int *sel, c128 *E, int64_t lde) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -402,7 +413,8 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
     return x ^ (x >> 31);
 }
-__global__ void k_randn(int64_t cnt, uint64_t seed, c128 *X) {
+// (real_only: N(0,1) real entries, the real starting block of a real pencil)
+__global__ void k_randn(int64_t cnt, uint64_t seed, c128 *X, int real_only) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= cnt) return;
     const uint64_t a = splitmix64(seed ^ (2 * (uint64_t)idx)), b = splitmix64(seed ^ (2 * (uint64_t)idx + 1));
@@ -410,7 +422,7 @@ __global__ void k_randn(int64_t cnt, uint64_t seed, c128 *X) {
     const double rad = sqrt(-2.0 * log(u1));
     double sn, cs;
     sincospi(2.0 * u2, &sn, &cs);
-    X[idx] = mk<double>(rad * cs * 0.7071067811865476, rad * sn * 0.7071067811865476);
+    X[idx] = real_only ? mk<double>(rad * cs, 0.0) : mk<double>(rad * cs * 0.7071067811865476, rad * sn * 0.7071067811865476);
 }
 
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
@@ -575,7 +587,8 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
         a.n = n; a.k = k; a.ldy = k; a.Y = Wc; a.nterm = 1;
         a.coef[0] = c128{1.0, 0.0}; a.X[0] = X; a.ldx[0] = ldx;
         launch_lincomb(a, st);
-        launch_colnorm2(n, k, Wc, k, nrm, st);
+        rc = colnorm2(h, k, Wc, k, nrm, st);
+        if (rc) return rc;
         k_normalize<<<nblk(blk), 256, 0, st>>>(n, (int)k, nrm, Wc, plane(0), nullptr, hld, 0);
         count_launch();
         // beta = sqrt(nrm): reuse the normalise kernel's formula on a k-vector
@@ -624,7 +637,8 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
         }
         // classical Gram-Schmidt with selective re-orthogonalisation (Kahan-Parlett / DGKS):
         // the second pass runs when some column lost more than 1/sqrt(2) of its norm
-        launch_colnorm2(n, k, Wv, k, nrm + k, st);
+        rc = colnorm2(h, k, Wv, k, nrm + k, st);
+        if (rc) return rc;
         for (int pass = 0; pass < 2; ++pass) {
             for (int j0 = 0; j0 <= i; j0 += JT) {
                 const int nj = std::min(JT, i + 1 - j0);
@@ -637,8 +651,8 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
             k_multiaxpy<<<nblk(blk), 256, 0, st>>>(n, (int)k, Vp, i + 1, hsp, Wv);
             count_launch();
             if (pass == 0) {
-                launch_colnorm2(n, k, Wv, k, nrm, st);
-                rc = cuda_check(cudaMemcpyAsync(hnorm.data(), nrm, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, st),
+                rc = colnorm2(h, k, Wv, k, nrm, st);
+                if (!rc) rc = cuda_check(cudaMemcpyAsync(hnorm.data(), nrm, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, st),
                                 "cgs norms");
                 if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "cgs norms");
                 if (rc) return rc;
@@ -647,7 +661,8 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
                 if (!again) break;
             }
         }
-        launch_colnorm2(n, k, Wv, k, nrm, st);
+        rc = colnorm2(h, k, Wv, k, nrm, st);
+        if (rc) return rc;
         k_normalize<<<nblk(blk), 256, 0, st>>>(n, (int)k, nrm, Wv, plane(i + 1), H, hld, i);
         count_launch();
         k_lsq_step<<<nblk((int64_t)pairs, 128), 128, 0, st>>>((int)k, ns, (const c128 *)w.shifts.p, H, hld, i, beta, S, mmax,
@@ -678,7 +693,7 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
     count_launch();
     k_zeta<<<nblk((int64_t)k * m), 256, 0, st>>>((int)k, ns, m, mmax, (const c128 *)w.zall.p, (c128 *)w.zeta.p);
     count_launch();
-    k_combine<<<nblk(blk), 256, 0, st>>>(n, (int)k, X, ldx, Vp, m, (const c128 *)w.zeta.p, Y, ldy);
+    k_combine<<<nblk(blk), 256, 0, st>>>(n, (int)k, X, ldx, Vp, m, (const c128 *)w.zeta.p, Y, ldy, h->realx ? 1 : 0);
     count_launch();
     rc = cuda_check(cudaGetLastError(), "gmres");
     if (rc) return rc;
@@ -695,7 +710,7 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
 
 // The columns of X are independent GMRES problems: process them in chunks whose Krylov
 // basis, (m_max + 1) n x chunk complex128 blocks, fits a memory budget (100 GiB, or 60%
-// of the free device memory if that is smaller).
+// of the free device memory if that is smaller), and of at most opts.gmres_chunk columns.
 int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st,
                 zolo_stats *stats) {
     const int mmax = std::max(1, h->opts.gmres_m_max > 0 ? h->opts.gmres_m_max : 100);
@@ -705,6 +720,7 @@ int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y
     const double per_col = (double)(mmax + 1) * h->n * sizeof(c128);
     int64_t chunk = std::max<int64_t>(1, (int64_t)(budget / per_col));
     if (chunk >= 32) chunk = chunk / 32 * 32;
+    if (h->opts.gmres_chunk > 0) chunk = std::min<int64_t>(chunk, h->opts.gmres_chunk);
     chunk = std::min(chunk, k);
     const int64_t nch = (k + chunk - 1) / chunk;
     chunk = (k + nch - 1) / nch;                        // balance the chunks
@@ -825,7 +841,31 @@ static int gram(zolo_factor_s *h, KrylovWork &w, int64_t n, int k, const c128 *Y
     return cuda_check(cudaGetLastError(), "gram");
 }
 
+// Y = R(B^-1 A) X for the handle's filter: Algorithm 2 (inner operator + shift-invariant
+// GMRES) for the Zolotarev filter, the inner operator alone for a contour-integral filter
+// (its quadrature points are all factored poles: r2 = 0).
+int filter_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st,
+                 zolo_stats *stats) {
+    if (h->fi.r2 > 0) return gmres_apply(h, k, X, ldx, Y, ldy, st, stats);
+    h->inner_failed = false;
+    const int rc = apply_inner(h, k, X, ldx, Y, ldy, st);
+    if (rc) h->inner_failed = true;
+    h->stats.n_gmres = 1;
+    h->stats.gmres_res = 0.0;
+    if (stats) {
+        stats->n_gmres = 1;
+        stats->gmres_res = 0.0;
+        stats->n_solv = (int64_t)h->r1 * k;
+    }
+    return rc;
+}
+
 // ---------------------------------------------------------------- Algorithm 1
+// Subspace iteration with Rayleigh-Ritz.  Real pencils with opts.real_block keep every block
+// real (one solve per pole).  With opts.lock, the pairs in (a, b) whose residual is <= tol
+// after an iteration are locked: they move to the front of the block and are not filtered
+// again, while every Rayleigh-Ritz step still runs on [locked | filtered] (the footnote of
+// Algorithm 1).  A converged Ritz value inside a declared eigengap returns ZOLO_EGAP.
 static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const c128 *X0, double *evals, c128 *evecs,
                          int64_t ldv, int64_t cap, int64_t *n_found, double *resid, zolo_stats *stats,
                          cudaStream_t st) {
@@ -847,24 +887,36 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
     if (!rc) rc = grow(h, w.Z, kk2);
     if (!rc) rc = grow(h, w.Qt, kk2);
     if (!rc) rc = grow(h, w.dvec, (size_t)k * sizeof(double));
+    if (!rc) rc = grow(h, w.idx, (size_t)k * sizeof(int));
     if (rc) return rc;
-    c128 *Q = (c128 *)w.Q.p, *Y = (c128 *)w.Y.p, *AY = (c128 *)w.AY.p, *BY = (c128 *)w.BY.p, *R = (c128 *)w.R.p;
+    c128 *Y = (c128 *)w.Y.p, *AY = (c128 *)w.AY.p, *BY = (c128 *)w.BY.p;
     c128 *At = (c128 *)w.At.p, *Bt = (c128 *)w.Bt.p, *U = (c128 *)w.U.p, *Wm = (c128 *)w.W.p;
     c128 *Ah = (c128 *)w.Ah.p, *Zm = (c128 *)w.Z.p, *Qt = (c128 *)w.Qt.p;
+    const bool real_pencil = pencil_is_real(h) && h->opts.real_block;
+    bool rx = false;
     if (X0) {
-        rc = cuda_check(cudaMemcpyAsync(Q, X0, blk * sizeof(c128), cudaMemcpyDeviceToDevice, st), "X0");
+        rc = cuda_check(cudaMemcpyAsync(w.Q.p, X0, blk * sizeof(c128), cudaMemcpyDeviceToDevice, st), "X0");
+        if (!rc && real_pencil) rc = block_is_real(h, k, (const c128 *)w.Q.p, k, st, &rx);
     } else {
-        k_randn<<<nblk(blk), 256, 0, st>>>(blk, h->opts.seed, Q);
+        k_randn<<<nblk(blk), 256, 0, st>>>(blk, h->opts.seed, (c128 *)w.Q.p, real_pencil ? 1 : 0);
         count_launch();
         rc = cuda_check(cudaGetLastError(), "randn");
+        rx = real_pencil;
     }
     if (rc) return rc;
+    struct ResetReal {
+        zolo_factor_s *h;
+        ~ResetReal() { h->realx = false; }
+    } reset_real{h};
+    h->realx = rx;
     const int itmax = std::max(1, h->opts.n_iter_max);
     const double tol = h->opts.tol > 0 ? h->opts.tol : 1e-10;
     const double drop = h->opts.drop_tol > 0 ? h->opts.drop_tol : 1e-14;
+    const bool lock = h->opts.lock != 0;
     std::vector<double> lam, res_all, mu;
     std::vector<int> sel;
-    int kq = k;
+    int kq = k;           // columns of the current block
+    int nl = 0;           // locked columns at its front
     int it = 0;
     bool converged = false;
     cudaEvent_t e0, e1, e2;
@@ -873,15 +925,22 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
     cudaEventCreate(&e2);
     float t_apply = 0.f, t_rr = 0.f;
     int n_gm = 0;
+    int64_t n_solv = 0;
     bool gmres_short = false;
     for (it = 1; it <= itmax; ++it) {
+        c128 *Q = (c128 *)w.Q.p, *R = (c128 *)w.R.p;
         cudaEventRecord(e0, st);
         // The first application starts from a random block: its filtered output is re-filtered
         // by the next iteration, so a loose GMRES tolerance (1e-6) is enough there; later
         // applications start from Ritz vectors and use gmres_tol.
         const double gt = h->opts.gmres_tol > 0 ? h->opts.gmres_tol : 1e-12;
         h->gmres_tol_now = (it == 1 && itmax > 1) ? std::max(gt, 1e-6) : gt;
-        rc = gmres_apply(h, kq, Q, kq, Y, kq, st, nullptr);          // Y = R(B^-1 A) Q
+        // Y = [Q_locked | R(B^-1 A) Q_rest]
+        if (nl > 0) {
+            k_copy_cols<<<nblk(n * nl), 256, 0, st>>>(n, nl, Q, kq, Y, kq);
+            count_launch();
+        }
+        rc = filter_apply(h, kq - nl, Q + nl, kq, Y + nl, kq, st, nullptr);
         h->gmres_tol_now = 0.0;
         if (rc == ZOLO_ENOCONV && !h->inner_failed) {               // GMRES step cap: use the block
             gmres_short = true;
@@ -889,6 +948,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         }
         if (rc) break;
         n_gm += h->stats.n_gmres;
+        n_solv += (int64_t)h->r1 * (kq - nl) * h->stats.n_gmres;
         cudaEventRecord(e1, st);
         launch_spmm(h->A, kq, Y, kq, AY, kq, c128{1.0, 0.0}, false, st);
         launch_spmm(h->B, kq, Y, kq, BY, kq, c128{1.0, 0.0}, false, st);
@@ -902,8 +962,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         for (double x : mu) mumax = std::max(mumax, x);
         // directions whose B-norm is at the level of the filtered block's own error are
         // noise: drop below max(drop_tol, (10 * GMRES tolerance of this pass)^2) * max mu
-        const double tol_it = (it == 1 && itmax > 1) ? std::max(h->opts.gmres_tol > 0 ? h->opts.gmres_tol : 1e-12, 1e-6)
-                                                     : (h->opts.gmres_tol > 0 ? h->opts.gmres_tol : 1e-12);
+        const double tol_it = (it == 1 && itmax > 1) ? std::max(gt, 1e-6) : gt;
         const double drop_it = std::max(drop, 100.0 * tol_it * tol_it);
         std::vector<int> keep;
         std::vector<double> scl;
@@ -914,8 +973,8 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
             }
         const int kt = (int)keep.size();
         if (h->opts.verbose)
-            std::fprintf(stderr, "[zolo] iteration %d: GMRES steps %d, B-Gram mu in [%.3e, %.3e], kept %d of %d\n", it,
-                         h->stats.n_gmres, *std::min_element(mu.begin(), mu.end()), mumax, kt, kq);
+            std::fprintf(stderr, "[zolo] iteration %d: %d locked, GMRES steps %d, B-Gram mu in [%.3e, %.3e], kept %d of %d\n",
+                         it, nl, h->stats.n_gmres, *std::min_element(mu.begin(), mu.end()), mumax, kt, kq);
         if (kt == 0) {
             rc = set_error(ZOLO_ENOCONV, "filtered block vanished (no eigenvalues in the interval?)");
             break;
@@ -931,7 +990,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         rc = gemm1(h, st, w.jobs, Wm, Zm, Qt, job(0, 1, kq, 0, 1, kt, 0, 1, kq, kq, kt, kt, 0));
         if (!rc) rc = gemm1(h, st, w.jobs, Y, Qt, Q, job(0, kq, 1, 0, 1, kq, 0, kt, 1, (int)n, kt, kq, 0));
         if (rc) break;
-        // sort the Ritz pairs ascending: permute the columns of Q through a gather on the host order
+        // the Ritz pairs ascending (a host order of the columns of Q)
         std::vector<int> ord(kt);
         std::iota(ord.begin(), ord.end(), 0);
         std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return lam[x] < lam[y]; });
@@ -948,9 +1007,10 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         rc = grow(h, w.nrm, (size_t)3 * kq * sizeof(double));
         if (rc) break;
         double *nr = (double *)w.nrm.p;
-        launch_colnorm2(n, kq, R, kq, nr, st);
-        launch_colnorm2(n, kq, Q, kq, nr + kq, st);
-        launch_colnorm2(n, kq, BY, kq, nr + 2 * kq, st);
+        rc = colnorm2(h, kq, R, kq, nr, st);
+        if (!rc) rc = colnorm2(h, kq, Q, kq, nr + kq, st);
+        if (!rc) rc = colnorm2(h, kq, BY, kq, nr + 2 * kq, st);
+        if (rc) break;
         std::vector<double> hn(3 * kq);
         rc = cuda_check(cudaMemcpyAsync(hn.data(), nr, 3 * kq * sizeof(double), cudaMemcpyDeviceToHost, st), "res");
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "res");
@@ -965,9 +1025,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         res_all.assign(kq, 0.0);
         double relerr = 0.0;
         const double ab = std::max(std::fabs(a), std::fabs(b));
-        for (int i = 0; i < kq; ++i) {
-            res_all[i] = std::sqrt(hn[i]) / (h->normA_inf * std::sqrt(std::max(hn[kq + i], 1e-300)));
-        }
+        for (int i = 0; i < kq; ++i) res_all[i] = std::sqrt(hn[i]) / (h->normA_inf * std::sqrt(std::max(hn[kq + i], 1e-300)));
         sel.clear();
         double worst = 0.0;
         for (int t = 0; t < kq; ++t) {
@@ -988,16 +1046,47 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
             converged = true;
             break;
         }
+        if (lock && it < itmax) {
+            // locked first (converged pairs in (a, b), ascending), then the rest ascending
+            std::vector<int> perm;
+            for (int t = 0; t < kq; ++t) {
+                const int i = ord[t];
+                if (lam[i] > a && lam[i] < b && res_all[i] <= tol) perm.push_back(i);
+            }
+            const int nlock = (int)perm.size();
+            for (int t = 0; t < kq; ++t) {
+                const int i = ord[t];
+                if (!(lam[i] > a && lam[i] < b && res_all[i] <= tol)) perm.push_back(i);
+            }
+            rc = cuda_check(cudaMemcpyAsync(w.idx.p, perm.data(), kq * sizeof(int), cudaMemcpyHostToDevice, st), "perm");
+            if (rc) break;
+            k_select_cols<<<nblk(n * kq), 256, 0, st>>>(n, kq, Q, kq, (const int *)w.idx.p, R, kq);
+            count_launch();
+            rc = cuda_check(cudaStreamSynchronize(st), "perm");
+            if (rc) break;
+            std::swap(w.Q, w.R);                          // the permuted block becomes Q
+            std::vector<double> l2(kq), r2(kq);
+            for (int t = 0; t < kq; ++t) {
+                l2[t] = lam[perm[t]];
+                r2[t] = res_all[perm[t]];
+            }
+            lam.swap(l2);
+            res_all.swap(r2);
+            nl = nlock;
+        } else {
+            nl = 0;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
     if (rc) return rc;
+    c128 *Q = (c128 *)w.Q.p;
     h->stats.n_iter = std::min(it, itmax);
     h->stats.t_apply_ms = t_apply;
     h->stats.t_rr_ms = t_rr;
     h->stats.n_gmres = n_gm;
-    h->stats.n_solv = (int64_t)h->r1 * k * n_gm;
+    h->stats.n_solv = n_solv;
     const int nf = (int)sel.size();
     h->stats.n_found = nf;
     *n_found = nf;
@@ -1007,8 +1096,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
         if (resid) resid[t] = res_all[sel[t]];
     }
     if (nf > 0 && evecs) {
-        rc = grow(h, w.idx, nf * sizeof(int));
-        if (!rc) rc = cuda_check(cudaMemcpyAsync(w.idx.p, sel.data(), nf * sizeof(int), cudaMemcpyHostToDevice, st), "sel");
+        rc = cuda_check(cudaMemcpyAsync(w.idx.p, sel.data(), nf * sizeof(int), cudaMemcpyHostToDevice, st), "sel");
         if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "sel");
         if (rc) return rc;
         k_select_cols<<<nblk(n * nf), 256, 0, st>>>(n, nf, Q, kq, (const int *)w.idx.p, evecs, ldv);
@@ -1019,6 +1107,18 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
     rc = cuda_check(cudaStreamSynchronize(st), "eigs");
     if (rc) return rc;
     if (stats) *stats = h->stats;
+    // a converged Ritz value strictly inside a declared eigengap (a-, a+) or (b-, b+)
+    // contradicts the gaps the filter was built on: the pairs near that end may be missing
+    if (h->fi.kind == ZOLO_FILTER_ZOLO) {
+        const double m = 1e-9 * (b - a);
+        const double *g = h->fi.gap;
+        for (int i = 0; i < kq; ++i) {
+            if (!(res_all[i] <= tol)) continue;
+            const double x = lam[i];
+            if ((x > g[0] + m && x < g[1] - m) || (x > g[2] + m && x < g[3] - m))
+                return set_error(ZOLO_EGAP, "converged Ritz value " + std::to_string(x) + " lies inside a declared eigengap");
+        }
+    }
     if (!converged)
         return set_error(ZOLO_ENOCONV, gmres_short ? "eigenpair residuals above tol (GMRES also hit gmres_m_max)"
                                                    : "eigenpair residuals above tol after n_iter_max iterations");
@@ -1041,7 +1141,12 @@ int zolo_apply(zolo_factor_h h, int64_t k, const void *X, int64_t ldx, void *Y, 
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
     h->stats.n_refine_max = 0;
-    int rc = gmres_apply(h, k, (const c128 *)X, ldx, (c128 *)Y, ldy, st, stats);
+    bool rx = false;
+    int rc = ZOLO_OK;
+    if (pencil_is_real(h) && h->opts.real_block) rc = block_is_real(h, k, (const c128 *)X, ldx, st, &rx);
+    h->realx = rx;
+    if (!rc) rc = filter_apply(h, k, (const c128 *)X, ldx, (c128 *)Y, ldy, st, stats);
+    h->realx = false;
     cudaEventRecord(e1, st);
     if (rc == ZOLO_OK || rc == ZOLO_ENOCONV) {
         int rc2 = cuda_check(cudaStreamSynchronize(st), "apply");
@@ -1074,6 +1179,10 @@ int zolo_eigs(const zolo_csr *A, const zolo_csr *B, double a, double b, int64_t 
               double *resid, zolo_stats *stats, void *stream) {
     clear_error();
     if (!A || !B || !evals || !n_found || !(a < b) || n_est < 0) return set_error(ZOLO_EINVAL, "bad argument");
+    CsrHost ha, hb;
+    int rc0 = csr_host_view(A, ha, &A);
+    if (!rc0) rc0 = csr_host_view(B, hb, &B);
+    if (rc0) return rc0;
     zolo_opts o;
     if (opts) o = *opts; else zolo_opts_default(&o);
     zolo_filter_spec fs;

@@ -1,17 +1,19 @@
 // zolo_solve_noalloc: the block solve of zolo_solve with its front workspaces taken from a
 // fixed, file-scope device array instead of device allocations.
 //
-// Who needs it: callers that must not allocate device memory on the calls they repeat --
-// code running inside a CUDA stream capture (cudaMalloc is not capturable), allocation-free
-// real-time loops, or hosts whose memory pool is owned by someone else.  They create the
-// factor handle and run one zolo_solve with their block width at set-up (both allocate);
-// afterwards this entry point allocates nothing.
+// Who needs it: callers that cannot call cudaMalloc on the calls they repeat -- hosts whose
+// device memory is managed by another component (a framework's caching allocator or a
+// memory pool that must own every byte), and allocation-free real-time loops, where an
+// allocation could block or fail part-way through.  They create the factor handle and run
+// one zolo_solve with their block width at set-up (both allocate); afterwards this entry
+// point allocates nothing.
 //
 // Limits: complex128 (ZOLO_PREC_FP64) handles only (the mixed-precision path needs
 // refinement buffers); (rows of all fronts + n) * k * 16 bytes must fit NOALLOC_BYTES.
 // The array is shared by every call and keeps the last call's contents: the workspaces are
 // cleared at the start of each call, and calls that overlap on the GPU (different streams,
-// or the same handle from several threads) race on it.
+// or the same handle from several threads) race on it.  The call is asynchronous: it
+// returns once its work is queued on `stream`; synchronise that stream before reading X.
 #include <cstring>
 #include "factor.h"
 
@@ -62,8 +64,14 @@ extern "C" int zolo_solve_noalloc(zolo_factor_h h, int32_t pole, int32_t herm, i
         return set_error(ZOLO_EINVAL, "workspace of " + std::to_string(wbytes + ybytes) +
                                           " bytes exceeds the fixed no-allocation array of " +
                                           std::to_string(NOALLOC_BYTES) + " bytes");
+    int cur = -1;
+    int rc = cuda_check(cudaGetDevice(&cur), "cudaGetDevice");
+    if (rc) return rc;
+    if (cur != h->device)           // the array is per device; the factors live on h->device
+        return set_error(ZOLO_EINVAL, "current device " + std::to_string(cur) + " is not the handle's device " +
+                                          std::to_string(h->device));
     void *base = nullptr;
-    int rc = scratch_address(&base);
+    rc = scratch_address(&base);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     c128 *W = (c128 *)base;
@@ -119,5 +127,6 @@ extern "C" int zolo_solve_noalloc(zolo_factor_h h, int32_t pole, int32_t herm, i
     run(h->bwd);
     rc = cuda_check(cudaGetLastError(), "solve_noalloc launch");
     if (rc) return rc;
-    return cuda_check(cudaStreamSynchronize(st), "solve_noalloc");
+    h->stats.solve_cols += k;
+    return ZOLO_OK;
 }

@@ -29,6 +29,10 @@ extern "C" int zolo_eigs_slices(const zolo_csr *A, const zolo_csr *B, int32_t ns
         if (!std::isfinite(bounds[s]) || (s > 0 && !(bounds[s - 1] < bounds[s])))
             return set_error(ZOLO_EINVAL, "slice bounds must be finite and strictly increasing");
     *n_found = 0;
+    CsrHost ha, hb;                                 // one host copy for every slice
+    int rc0 = csr_host_view(A, ha, &A);
+    if (!rc0) rc0 = csr_host_view(B, hb, &B);
+    if (rc0) return rc0;
     zolo_opts o;
     if (opts) o = *opts; else zolo_opts_default(&o);
 

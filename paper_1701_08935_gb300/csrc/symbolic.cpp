@@ -376,8 +376,12 @@ int zolo_analyze(const zolo_csr *A, const zolo_csr *B, const zolo_opts *opts, zo
     clear_error();
     if (!out) return set_error(ZOLO_EINVAL, "null output");
     *out = nullptr;
+    CsrHost ha, hb;
+    int st = csr_host_view(A, ha, &A);
+    if (!st) st = csr_host_view(B, hb, &B);
+    if (st) return st;
     bool ca, cb;
-    int st = check_csr(A, "A", ca);
+    st = check_csr(A, "A", ca);
     if (st) return st;
     st = check_csr(B, "B", cb);
     if (st) return st;

@@ -29,8 +29,9 @@ int zolo_build(int r, double ell, Zolo &z);
 
 struct zolo_filter_s {
     zolo_filter_spec spec;
+    int kind = ZOLO_FILTER_ZOLO;
     zolo::Zolo inner, outer;
-    double alpha, beta, gamma, ell1, ell2, delta0;
+    double alpha = 0, beta = 0, gamma = 0, ell1 = 0, ell2 = 0, delta0 = 0;
     zolo_filter_info info;
     double eval(double x) const;
 };
@@ -54,6 +55,17 @@ struct zolo_symbolic_s {
 };
 
 namespace zolo {
+// Host copy of a CSR given in device memory or with complex64 values.
+struct CsrHost {
+    zolo_csr c;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> v;
+};
+// *use = `in` itself when it is a host CSR of double / complex double values, else a host
+// complex128 / double copy held by `buf`.  EINVAL for an unknown mem or dtype, ECUDA when a
+// device copy fails.
+int csr_host_view(const zolo_csr *in, CsrHost &buf, const zolo_csr **use);
 // Validate a host CSR; fills `complex_` with whether it carries complex values.
 int check_csr(const zolo_csr *M, const char *name, bool &complex_);
 // Build the symbolic analysis of pattern(A) U pattern(B).

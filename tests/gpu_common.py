@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import eigs as E
-from paper_1701_08935_gb300 import synth
+import synth
 
 torch = pytest.importorskip("torch")
 

@@ -8,7 +8,7 @@ import pytest
 import scipy.sparse as sp
 
 import paper_1701_08935_gb300 as Z
-from paper_1701_08935_gb300 import synth
+import synth
 
 HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "zolo.h")
 
@@ -88,3 +88,12 @@ def test_slices_reject_bad_bounds_before_any_device_work():
         rc = Z.lib.zolo_eigs_slices(C.byref(hA.s), C.byref(hB.s), len(bd) - 1, bd.ctypes.data, C.byref(o),
                                     ev.ctypes.data, C.c_void_p(1), 4, 4, C.byref(nf), None, None, None, None)
         assert rc == Z.EINVAL
+
+
+def test_short_blocks_refused_before_any_launch():
+    """The binding checks block shapes itself (the C ABI receives bare pointers)."""
+    Z.check_block((10, 3), "X", 10)
+    Z.check_block((10, 3), "out", 10, 3)
+    for shape, k in (((9, 3), None), ((10, 2), 3), ((10, 0), None), ((10,), None)):
+        with pytest.raises(ValueError):
+            Z.check_block(shape, "X", 10, k)

@@ -8,7 +8,7 @@ from oracle import apply as AP
 from oracle import factor as FA
 from oracle import filter as F
 from gpu_common import CASES, case, colrel, dev, host, need_gpu
-from paper_1701_08935_gb300 import synth
+import synth
 
 pytestmark = pytest.mark.gpu
 

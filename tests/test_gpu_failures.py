@@ -6,7 +6,7 @@ import scipy.sparse as sp
 
 import paper_1701_08935_gb300 as Z
 from gpu_common import case, colrel, dev, host, need_gpu
-from paper_1701_08935_gb300 import synth
+import synth
 
 pytestmark = pytest.mark.gpu
 

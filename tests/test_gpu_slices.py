@@ -7,7 +7,7 @@ import pytest
 import paper_1701_08935_gb300 as Z
 from oracle import eigs as E
 from gpu_common import host, need_gpu
-from paper_1701_08935_gb300 import synth
+import synth
 
 pytestmark = pytest.mark.gpu
 

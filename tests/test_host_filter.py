@@ -95,3 +95,53 @@ def test_bad_orders_rejected():
     for r in [(17, 2), (2, 17)]:
         with pytest.raises(Z.ZoloError):
             Z.Filter(0.0, 1.0, 2.0, 3.0, *r)
+
+
+@pytest.mark.parametrize("gaps", [(-1.1, -0.9, 0.9, 1.1), (0.1, 0.3, 2.0, 2.5), (-math.inf, 0.5, 1.5, 1.6)])
+def test_order_table_matches_oracle(gaps):
+    t = Z.filter_table(*gaps, 3)
+    g = F.delta0_table(*gaps, 3)
+    # the oracle's extrema come from a numerical search: ~1e-5 relative at delta0 ~ 1e-10
+    assert np.allclose(t, g, rtol=1e-4, atol=1e-15)
+    assert np.allclose(t, t.T, rtol=1e-10, atol=1e-15)           # Theorem 2: only r1 r2 matters
+
+
+def test_order_selection_modes():
+    """Orders from eps (Remark after Algorithm 2): r1 fixed -> smallest r2; r2 fixed ->
+    smallest r1; both free -> smallest r = r1 = r2, all read off the table."""
+    gaps = (-1.1, -0.9, 0.9, 1.1)
+    t = Z.filter_table(*gaps, 8)
+    eps = 1e-9
+    f = Z.Filter(*gaps, 2, 0, eps)
+    want = 1 + int(np.argmax(t[1, :] <= eps))
+    assert (f.r1, f.r2) == (2, want)
+    assert f.info.delta0 <= eps < t[1, want - 2]
+    f = Z.Filter(*gaps, 0, 3, eps)
+    want = 1 + int(np.argmax(t[:, 2] <= eps))
+    assert (f.r1, f.r2) == (want, 3)
+    f = Z.Filter(*gaps, 0, 0, eps)
+    d = np.diag(t)
+    assert f.r1 == f.r2 == 1 + int(np.argmax(d <= eps))
+    assert f.info.gap[0] == -1.1 and f.info.gap[3] == 1.1
+
+
+@pytest.mark.parametrize("kind", ["CITZ", "CIGQ"])
+@pytest.mark.parametrize("npoles", [2, 6, 16, 32])
+def test_contour_filters_match_oracle(kind, npoles):
+    a, b = 0.3, 1.7
+    p = Z.ContourFilter(getattr(Z, "FILTER_" + kind), a, b, npoles)
+    o = F.ContourFilter(kind, a, b, npoles)
+    x = np.linspace(-1.0, 3.0, 401)
+    assert np.allclose(p(x), o(x), rtol=1e-12, atol=1e-13)
+    assert p.r1 == npoles // 2 and p.r2 == 0 and p.info.kind == getattr(Z, "FILTER_" + kind)
+    order = lambda z: np.argsort(z.real + 1e-3 * z.imag)
+    assert np.allclose(p.sigma_hat[order(p.sigma_hat)], o.sigma_hat[order(o.sigma_hat)], rtol=1e-14, atol=1e-14)
+    assert np.allclose(p.w_hat[order(p.sigma_hat)], o.w_hat[order(o.sigma_hat)], rtol=1e-12, atol=1e-15)
+
+
+def test_contour_filter_arguments_rejected():
+    for args in ((Z.FILTER_CITZ, 1.0, 0.0, 4), (Z.FILTER_CIGQ, 0.0, 1.0, 3), (Z.FILTER_CITZ, 0.0, 1.0, 0),
+                 (Z.FILTER_CITZ, 0.0, 1.0, 2 * Z.MAX_R + 2), (7, 0.0, 1.0, 4)):
+        with pytest.raises(Z.ZoloError) as e:
+            Z.ContourFilter(*args)
+        assert e.value.status == Z.EINVAL

@@ -5,7 +5,7 @@ import scipy.sparse as sp
 
 import paper_1701_08935_gb300 as Z
 from oracle import ordering as O
-from paper_1701_08935_gb300 import synth
+import synth
 
 
 def _compare(p, leaf, graph=False):

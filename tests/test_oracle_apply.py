@@ -6,7 +6,7 @@ import pytest
 from oracle import apply as AP
 from oracle import eigs as E
 from oracle import filter as F
-from paper_1701_08935_gb300 import synth
+import synth
 
 
 def _setup(kind):

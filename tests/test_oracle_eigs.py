@@ -9,7 +9,7 @@ import scipy.sparse as sp
 from oracle import apply as AP
 from oracle import eigs as E
 from oracle import filter as F
-from paper_1701_08935_gb300 import synth
+import synth
 
 
 def _closed_form_2d(n, w=0.1):
@@ -119,3 +119,37 @@ def test_subspace_iteration_converges_at_the_filter_ratio():
     measured = (errs[7] / errs[3]) ** 0.25          # geometric mean over iterations 4..8
     assert 0.1 < theory < 0.25                          # the weak-filter regime the test needs
     assert theory / 1.5 <= measured <= theory * 1.5, (measured, theory)
+
+
+def test_relerr_and_residual_hand_values():
+    """e_{Lambda,X} (eq. relerr, Section 3) and the residual metric on a 2 x 2 diagonal pencil
+    worked by hand.  A = diag(2, 5), B = diag(1, 4), ||A||_inf = 5; a = -4, b = 3 so that
+    max(|a|, |b|) = 4 differs from max(a, b) = 3.
+      x1 = (1, 0), lam = 2.1:  A x - lam B x = (-0.1, 0),  ||x|| = 1, ||B x|| = 1
+      x2 = (0, 2), lam = 1.3:  A x - lam B x = (0, -0.4),  ||x|| = 2, ||B x|| = 8
+    e per column: 0.1 / (4 * 1) = 0.025 and 0.4 / (4 * 8) = 0.0125, max 0.025.
+    residual per column: 0.1 / (5 * 1) = 0.02 and 0.4 / (5 * 2) = 0.04.
+    A denominator with ||x|| instead of ||B x|| gives 0.05 for x2, one with max(a, b)
+    gives 0.0333 for x1, so either mistake fails."""
+    A = sp.diags([2.0, 5.0]).tocsr()
+    B = sp.diags([1.0, 4.0]).tocsr()
+    X = np.array([[1.0, 0.0], [0.0, 2.0]], dtype=np.complex128)
+    lam = np.array([2.1, 1.3])
+    assert E.relerr(A, B, lam[:1], X[:, :1], -4.0, 3.0) == pytest.approx(0.025, rel=1e-14)
+    assert E.relerr(A, B, lam[1:], X[:, 1:], -4.0, 3.0) == pytest.approx(0.0125, rel=1e-14)
+    assert E.relerr(A, B, lam, X, -4.0, 3.0) == pytest.approx(0.025, rel=1e-14)
+    assert np.allclose(E.residuals(A, B, lam, X), [0.02, 0.04], rtol=1e-14)
+
+
+def test_relerr_and_residual_complex_hand_values():
+    """The same metrics on a complex Hermitian pencil, by hand:
+    A = [[2, i], [-i, 2]] (||A||_inf = 3), B = diag(1, 2), x = (1, i), lam = 1:
+    A x = (2 + i*i, -i + 2i) = (1, i), B x = (1, 2i), A x - lam B x = (0, -i), norm 1;
+    ||x|| = sqrt 2, ||B x|| = sqrt 5.  With (a, b) = (-1, 0.5): e = 1 / sqrt 5,
+    residual = 1 / (3 sqrt 2)."""
+    A = sp.csr_matrix(np.array([[2.0, 1j], [-1j, 2.0]]))
+    B = sp.diags([1.0, 2.0]).tocsr()
+    X = np.array([[1.0], [1j]])
+    lam = np.array([1.0])
+    assert E.relerr(A, B, lam, X, -1.0, 0.5) == pytest.approx(1.0 / math.sqrt(5.0), rel=1e-14)
+    assert E.residuals(A, B, lam, X)[0] == pytest.approx(1.0 / (3.0 * math.sqrt(2.0)), rel=1e-14)

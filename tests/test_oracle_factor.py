@@ -6,7 +6,7 @@ import scipy.linalg as sla
 from oracle import factor as FA
 from oracle import filter as F
 from oracle import ordering as O
-from paper_1701_08935_gb300 import synth
+import synth
 
 
 def test_lu_nopivot_definition():

@@ -217,3 +217,53 @@ def test_zolo_c_reflection_identities(r, ell):
     x = np.linspace(1e-3, 1.0, 50)
     assert np.all(F.zolo_product(x, c) > 0)
     assert np.allclose(F.zolo_product(-x, c), -F.zolo_product(x, c), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("npoles", [2, 4, 8, 16])
+def test_citz_closed_form(npoles):
+    """Trapezoidal rule on the circle through a, b with nodes at 2 pi (j - 1/2)/p: the nodes
+    zeta_j = e^{i theta_j} are the roots of zeta^p = -1, and the partial fractions of
+    1/(1 + s^p) are sum_j (zeta_j / p) / (zeta_j - s) (residue 1/(p zeta_j^(p-1)) = -zeta_j/p).
+    So CITZ(p)(x) = 1 / (1 + ((x - c)/rho)^p) exactly (Section 1.1's trapezoidal filter)."""
+    a, b = 0.3, 1.7
+    f = F.ContourFilter("CITZ", a, b, npoles)
+    x = np.linspace(-2.0, 4.0, 241)
+    s = (x - 0.5 * (a + b)) / (0.5 * (b - a))
+    assert np.allclose(f(x), 1.0 / (1.0 + s ** npoles), rtol=1e-13, atol=1e-15)
+    assert len(f.sigma_hat) == npoles // 2 and np.all(f.sigma_hat.imag > 0)
+
+
+def test_cigq_pins():
+    """Gauss-Legendre contour filter: the integrand at the centre is the constant 1/(2 pi)
+    in theta, integrated exactly (R(c) = 1); the rule is symmetric about the centre; with
+    many points it converges to the indicator of (a, b) away from the contour and to the
+    principal value 1/2 on it (a and b sit at theta = pi, 0, the ends of both half rules)."""
+    a, b = -1.0, 3.0
+    c, rho = 1.0, 2.0
+    f = F.ContourFilter("CIGQ", a, b, 8)
+    assert f(np.array([c]))[0] == pytest.approx(1.0, abs=1e-14)
+    x = np.linspace(-4, 6, 101)
+    assert np.allclose(f(x), f(2 * c - x), atol=1e-14)
+    g = F.ContourFilter("CIGQ", a, b, 96)
+    inside = np.array([c - 0.5 * rho, c + 0.5 * rho, c + 0.3 * rho])
+    outside = np.array([c - 2 * rho, c + 2 * rho, c + 5 * rho])
+    assert np.max(np.abs(g(inside) - 1.0)) < 1e-12
+    assert np.max(np.abs(g(outside))) < 1e-12
+    assert np.allclose(g(np.array([a, b])), 0.5, atol=1e-10)
+    # wrong half-weight (pi/2 -> pi) would double R(c)
+    assert len(g.sigma_hat) == 48
+
+
+def test_delta0_table_depends_on_r1_r2_product():
+    """Theorem 2: S(x; l1) = Z_{(2r1)(2r2)}(x; l1), so the error delta0 of the Remark after
+    Algorithm 2 depends on (r1, r2) only through r1 r2: the table is symmetric and
+    delta0(1, 4) = delta0(2, 2) = delta0(4, 1); it decreases along rows and columns."""
+    gaps = (-1.1, -0.9, 0.9, 1.1)
+    t = F.delta0_table(*gaps, 4)
+    assert np.allclose(t, t.T, rtol=1e-6, atol=1e-15)      # (1 - S)/2 carries ~1e-16 absolute
+    assert t[0, 3] == pytest.approx(t[1, 1], rel=1e-6)
+    assert t[3, 0] == pytest.approx(t[1, 1], rel=1e-6)
+    assert np.all(np.diff(t, axis=0) < 0) and np.all(np.diff(t, axis=1) < 0)
+    # and the entries are the composite function's error at l1 (the Remark): (1 - S(l1))/2
+    f = F.ZoloFilter(*gaps, 2, 3)
+    assert t[1, 2] == pytest.approx(0.5 * (1.0 - float(f.S(f.ell1))), rel=1e-12)

@@ -17,7 +17,7 @@ from oracle import apply as AP
 from oracle import eigs as E
 from oracle import factor as FA
 from oracle import filter as F
-from paper_1701_08935_gb300 import synth
+import synth
 
 
 def _case():

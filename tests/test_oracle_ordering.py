@@ -7,7 +7,7 @@ import pytest
 import scipy.sparse as sp
 
 from oracle import ordering as O
-from paper_1701_08935_gb300 import synth
+import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 

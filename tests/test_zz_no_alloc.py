@@ -1,5 +1,6 @@
 """zolo_solve_noalloc -- the block solve for callers that must not allocate device memory
-on repeated calls (stream capture, allocation-free loops) -- gives the same result as
+on repeated calls (hosts whose device memory belongs to another component, allocation-free
+loops) -- gives the same result as
 zolo_solve, on two calls in a row with different right-hand sides.  Kept in a file that
 pytest collects last."""
 import numpy as np
@@ -7,7 +8,7 @@ import pytest
 
 import paper_1701_08935_gb300 as Z
 from gpu_common import case, colrel, dev, host, need_gpu
-from paper_1701_08935_gb300 import synth
+import synth
 
 pytestmark = pytest.mark.gpu
 
