@@ -252,7 +252,7 @@ int  zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbo
  * of the same no-pivot multifrontal factorisation (eq. IGEVP footnote: n_lambda is only
  * estimated; counts at a and b give it).  Always complex128 fronts whatever
  * opts->precision says (complex64 pivot signs are unreliable for indefinite shifts);
- * nshift >= 1 shifts, factored in batches of at most ZOLO_MAX_R that fit 45% of the
+ * nshift >= 1 shifts, factored in batches of at most ZOLO_MAX_R that fit 70% of the
  * free device memory.  A shift on an eigenvalue gives ESINGULAR.  Synchronises.     */
 int  zolo_inertia(const zolo_csr *A, const zolo_csr *B, zolo_symbolic sym, const zolo_opts *opts,
                   int32_t nshift, const double *sigma, int64_t *count, void *stream);

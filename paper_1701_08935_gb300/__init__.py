@@ -411,7 +411,7 @@ class Factor:
             _blk(X0, "X0", self.n, k0)
         rc = lib.zolo_eigs_factored(self.h, a, b, k0, x0, evals.ctypes.data, _vp(V.data_ptr()), cap, cap,
                                     C.byref(nf), resid.ctypes.data, C.byref(st), _stream(stream))
-        if rc not in (OK, ENOCONV):
+        if rc not in (OK, ENOCONV, EGAP):       # these still return the pairs found
             _check(rc, "zolo_eigs_factored")
         m = int(nf.value)
         return evals[:m], V[:, :m], resid[:m], st.as_dict(), rc

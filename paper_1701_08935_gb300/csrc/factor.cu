@@ -563,6 +563,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                     std::memset(&g, 0, sizeof(g));
                     g.bm = L.bm;
                     g.bn = L.bn;
+                    g.real = h->real_fac ? 1 : 0;
                     for (int z = 0; z < ni; ++z) {
                         g.jobs[z] = h->d_fjobs + L.off;
                         g.tmap[z] = L.tmoff >= 0 ? h->d_ftmap + L.tmoff : nullptr;
@@ -578,7 +579,9 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                 gemm(S.panelU, 1, 0);   // U12 = Linv A12
                 gemm(S.schur, 0, 0);    // A22 -= L21 U12
             }
-            // pivot-block inverses of this level's fronts
+            // pivot-block inverses of this level's fronts (the solves use them; an inertia
+            // count needs the pivots only)
+            if (h->count_neg) continue;
             for (int z = 0; z < ni; ++z) {
                 rc = cuda_check(cudaMemsetAsync(finv[z] + F.finv_lo, 0, (F.finv_hi - F.finv_lo) * eb, st), "memset inv");
                 if (rc) return rc;
@@ -1178,11 +1181,14 @@ static int factor_create(const zolo_csr *A, const zolo_csr *B, const zolo_filter
     if (!rc) rc = upload_csr(h, B, h->B);
     if (!rc) rc = build_factor_plan(h, A, B);
     if (!rc && count_neg) rc = dev_alloc(h, h->r1 * sizeof(int), (void **)&h->d_negcnt);
+    // a real pencil at real shifts (inertia counts) factors real matrices: one FMA per product
+    h->real_fac = count_neg && h->prec == ZOLO_PREC_FP64 && h->A.vr && h->B.vr;
+    for (int j = 0; j < h->r1; ++j) h->real_fac = h->real_fac && fi.sigma_hat[2 * j + 1] == 0.0;
     const size_t eb = elem_bytes(h->prec);
     for (int j = 0; !rc && j < h->r1; ++j) {
         rc = dev_alloc(h, h->pool_elems * eb, &h->pool[j]);
         if (!rc) rc = dev_alloc(h, std::max<int64_t>(1, h->inv_elems) * eb, &h->inv[j]);
-        if (!rc) rc = dev_alloc(h, std::max<int64_t>(1, h->finv_elems) * eb, &h->finv[j]);
+        if (!rc) rc = dev_alloc(h, (count_neg ? 1 : std::max<int64_t>(1, h->finv_elems)) * eb, &h->finv[j]);
     }
     h->stats.flops_factor = h->sym.info.flops_lu * h->r1;
     h->stats.flops_solve = 16.0 * (double)h->sym.info.nnz_factor;     // fwd + bwd, complex, per column
@@ -1231,7 +1237,7 @@ int zolo_inertia(const zolo_csr *A, const zolo_csr *B, zolo_symbolic sym, const 
     cudaMemGetInfo(&fr, &tot);
     const double per_shift = (double)S->info.front_entries * sizeof(c128);
     int batch = (int)std::max(1.0, std::min((double)std::min(nshift, ZOLO_MAX_R),
-                                             0.45 * (double)fr / std::max(per_shift, 1.0)));
+                                             0.7 * (double)fr / std::max(per_shift, 1.0)));
     for (int i0 = 0; i0 < nshift; i0 += batch) {
         const int nb = std::min(batch, nshift - i0);
         zolo_filter_info fi;

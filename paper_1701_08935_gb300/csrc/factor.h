@@ -114,6 +114,7 @@ struct zolo_factor_s {
     bool inner_failed = false;                     // an inner solve of the current GMRES failed
     int *d_negcnt = nullptr;                       // inertia: negative pivots per pole
     bool count_neg = false;
+    bool real_fac = false;                         // real matrices (real pencil, real shifts)
     zolo_stats stats;
 };
 
