@@ -927,6 +927,7 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
     int n_gm = 0;
     int64_t n_solv = 0;
     bool gmres_short = false;
+    bool empty_before = false;
     for (it = 1; it <= itmax; ++it) {
         c128 *Q = (c128 *)w.Q.p, *R = (c128 *)w.R.p;
         cudaEventRecord(e0, st);
@@ -1042,6 +1043,20 @@ static int eigs_factored(zolo_factor_s *h, double a, double b, int64_t k0, const
             std::fprintf(stderr, "[zolo] iteration %d: Ritz values in [%.6f, %.6f], %d inside (a, b), worst residual %.3e\n",
                          it, *std::min_element(lam.begin(), lam.end()), *std::max_element(lam.begin(), lam.end()),
                          (int)sel.size(), worst);
+        // An empty selection after the first application is not convergence: a random start
+        // block leaves the filter's equiripple tail on every direction outside (a, b), which
+        // drags the Rayleigh quotients of a narrow interval's pairs outside it; accept "no
+        // eigenvalue in (a, b)" only when two applications in a row find none.
+        if (sel.empty()) {
+            if (empty_before) {
+                converged = true;
+                break;
+            }
+            empty_before = true;
+            nl = 0;
+            continue;
+        }
+        empty_before = false;
         if (worst <= tol) {
             converged = true;
             break;

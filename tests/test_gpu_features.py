@@ -184,8 +184,8 @@ def test_device_csr_input(dtype):
         win = (40, 70)
         gaps = (lam[win[0] - 1], lam[win[0]], lam[win[1] - 1], lam[win[1]])
     a, b = 0.5 * (gaps[0] + gaps[1]), 0.5 * (gaps[2] + gaps[3])
-    spec = Z.FilterSpec(*gaps, 2, 2, 0.0)
-    opts = Z.default_opts(grid=pen.dims, leaf_max=leaf, n_iter_max=4)
+    spec = Z.FilterSpec(*gaps, 2, 3, 0.0)
+    opts = Z.default_opts(grid=pen.dims, leaf_max=leaf, n_iter_max=6)
     n_est = int(np.sum((lam > a) & (lam < b)))
     dA, keepA = _dev_csr(A, getattr(Z, dtype))
     dB, keepB = _dev_csr(B, getattr(Z, dtype))
