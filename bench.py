@@ -44,7 +44,7 @@ WORKLOADS = {
     "lap96": dict(
         recipe=("real3d", 96, 3, 2.0), lo=100, hi=120, r=(2, 2), k=32, n_iter=3,
         gmres_tol=1e-11, m_max=160, probe=(0.05, 1.2),
-        gaps=None,
+        gaps=(0.8730405097290543, 0.8734520855543522, 98, 0.8773074920364574, 0.8777089553145421, 117),
         desc="lap3d_96^3 real pencil (7-pt Laplacian + U[0,2], B = I + 0.1 M1x), ~20 eigenvalues near "
              "number 100, r=(2,2), k=32, <= 3 subspace iterations",
         cpu=("real3d", 12, 3, 2.0)),
