@@ -91,6 +91,8 @@ thread_local int g_plan_tc = ZOLO_TC_AUTO;
 thread_local std::vector<int32_t> *g_plan_tmap = nullptr;
 // Smallest inner extent of an accumulating product that add_gemm may split (zolo_opts.split_k_min).
 thread_local int g_plan_split_min = 512;
+// Instances (grid.z) the launches being planned will run with: they share the waves.
+thread_local int g_plan_ninst = 1;
 // Complex64 launches whose jobs average at least this many rows go to the tensor cores.
 constexpr double TC_MIN_ROWS = 128.0;
 
@@ -134,7 +136,7 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
     for (const GJob &j : jobs)
         if (j.m > 0 && j.n > 0 && j.k > 0) base += tiles_of(j);
     int factor = 1;
-    if (allow_split && base > 0 && L.tc && base < 8 * 152) {
+    if (allow_split && base > 0 && L.tc && base * g_plan_ninst < 8 * 152) {
         // two CTAs per SM: model the launch as waves x (k-stages of 8 of the longest slice +
         // ~8 stages of prologue and epilogue) and take the split that minimises it
         double best = 1e300;
@@ -147,16 +149,24 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
                     t += (int64_t)tiles_of(j) * ks;
                     stages = std::max(stages, ((j.k + ks - 1) / ks + 7) / 8);
                 }
-            const double cost = std::ceil((double)t / 304.0) * (stages + 8);
+            const double cost = std::ceil((double)t * g_plan_ninst / 304.0) * (stages + 8);
             if (cost < best * (1.0 - 1e-9)) {
                 best = cost;
                 factor = f;
             }
         }
-    } else if (allow_split && base > 0 && base < 4 * 152) {
-        factor = (4 * 152 + base - 1) / base;
+    } else if (allow_split && base > 0 && base * g_plan_ninst < 4 * 152) {
+        factor = (4 * 152 + base * g_plan_ninst - 1) / (base * g_plan_ninst);
     }
     int tiles = 0;
+    if (L.tc) {                            // the tile width the tensor-core kernel derives per job
+        L.wmax = 16;
+        for (const GJob &j : jobs)
+            if (j.m > 0 && j.n > 0 && j.k > 0) {
+                const int ntn = (j.n + 127) / 128;
+                L.wmax = std::max(L.wmax, ((j.n + ntn - 1) / ntn + 15) / 16 * 16);
+            }
+    }
     for (GJob j : jobs) {
         if (j.m <= 0 || j.n <= 0 || j.k <= 0) continue;
         j.tm = (j.m + L.bm - 1) / L.bm;
@@ -563,6 +573,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                     std::memset(&g, 0, sizeof(g));
                     g.bm = L.bm;
                     g.bn = L.bn;
+                    g.wmax = L.wmax;
                     g.real = h->real_fac ? 1 : 0;
                     for (int z = 0; z < ni; ++z) {
                         g.jobs[z] = h->d_fjobs + L.off;
@@ -599,6 +610,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                 std::memset(&g, 0, sizeof(g));
                 g.bm = L.bm;
                 g.bn = L.bn;
+                g.wmax = L.wmax;
                 for (int z = 0; z < ni; ++z) {
                     g.jobs[z] = h->d_fjobs + L.off;
                     g.tmap[z] = L.tmoff >= 0 ? h->d_ftmap + L.tmoff : nullptr;
@@ -661,6 +673,11 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
     g_plan_c64 = (h->prec == ZOLO_PREC_MIXED);
     g_plan_tc = h->opts.tensor_core;
     g_plan_split_min = h->opts.split_k_min > 0 ? h->opts.split_k_min : 512;
+    // a real pencil's real blocks run one instance per pole, otherwise K^-1 and K^-H per pole
+    g_plan_ninst = std::min(MAX_INST, (pencil_is_real(h) && h->opts.real_block) ? h->r1 : 2 * h->r1);
+    struct ResetNinst {
+        ~ResetNinst() { g_plan_ninst = 1; }
+    } reset_ninst;
     std::vector<int32_t> stm;
     g_plan_tmap = &stm;
     struct ClearMap {
@@ -820,6 +837,7 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                 double fl = 0.0;
                 g.bm = o.L.bm;
                 g.bn = o.L.bn;
+                g.wmax = std::max(o.L.wmax, o.LH.wmax);
                 auto base = [&](int kind, int z) -> cx<T> * {
                     switch (kind) {
                         case BK_POOL: return (cx<T> *)h->pool[pole[z]];

@@ -15,6 +15,7 @@ struct Launch {
     int bm = 64;         // GEMM tile height of the launch
     int bn = 64;         // GEMM tile width
     bool tc = false;     // complex64 tensor-core kernel (bm = bn = 128)
+    int wmax = 128;      // tensor-core launches: widest C tile of any job
     int64_t tmoff = -1;  // first entry of the launch's tile -> job map (-1: none)
 };
 

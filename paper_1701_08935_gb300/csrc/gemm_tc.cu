@@ -18,14 +18,17 @@
 // steps was measured either way).
 //
 // Tiles: one CTA per 128 x w tile of C, w <= 128 columns chosen per job so that the
-// ceil(n / 128) column tiles have equal width (a multiple of 16).  Two CTAs share an SM, so
-// the global-memory latencies of one (job lookup, first stages, epilogue) overlap the MMAs of
-// the other: each allocates 256 tensor-memory columns (Cr in [0, 128), Ci in [128, 256)) and
-// 96 KB of shared memory, three stages of k = 8.  All 256 threads stage the operands (global
-// loads, conjugation, hi/lo split, 16-byte stores in the canonical no-swizzle K-major layout,
-// each quarter-warp writing 128 contiguous bytes); one elected thread issues the MMAs of a
-// stage and commits them to the stage's mbarrier, and a buffer is refilled once the MMAs of
-// the stage that used it have completed, two stages later.  Every wait on an mbarrier is
+// ceil(n / 128) column tiles have equal width (a multiple of 16).  Two CTAs share an SM;
+// each allocates 256 tensor-memory columns (Cr in [0, 128), Ci in [128, 256)).
+//
+// Pipeline: the operands stream through a ring of P raw stages (k = 8 complex each) filled
+// by cp.async (8-byte copies with zero fill at the edges, so no thread waits on a global
+// load); P - 1 stages are in flight while one is converted.  Each step converts the oldest
+// raw stage (conjugation, hi/lo split) into one of two MMA stages in the canonical
+// no-swizzle K-major layout, and one elected thread issues that stage's MMAs and commits
+// them to its mbarrier; an MMA stage is overwritten once the MMAs that read it (two steps
+// earlier) have completed.  P depends on the widest tile of the launch (WMAX = 32, 64, 128:
+// P = 6, 5, 3) so that two CTAs fit an SM's shared memory.  Every wait on an mbarrier is
 // bounded in time (2 s): on expiry the CTA skips its remaining waits and its epilogue,
 // records ZOLO_ETIMEOUT in a device status word (read by gemm_tc_status) and releases its
 // tensor memory.
@@ -41,13 +44,22 @@ namespace {
 constexpr int TC_BM = 128;                 // rows of a C tile (MMA M)
 constexpr int TC_BN = 128;                 // widest C tile (MMA N)
 constexpr int TC_BK = 8;                   // complex k-extent of a stage (one MMA k-step)
-constexpr int TC_NSTAGE = 3;               // shared-memory stages
 constexpr int TC_PLANE_A = TC_BM * TC_BK * 4;        // bytes of one A plane (4 KB)
-constexpr int TC_PLANE_B = TC_BN * TC_BK * 4;        // bytes of one B plane (4 KB)
-constexpr int TC_STAGE = 4 * TC_PLANE_A + 4 * TC_PLANE_B;   // 32 KB
-constexpr int TC_SMEM = TC_NSTAGE * TC_STAGE + 64;          // + mbarriers, TMEM slot, job index
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;              // 2 s per mbarrier wait at most
+
+// Shared-memory plan of a launch whose tiles are at most WMAX wide.
+template <int WMAX> struct TcPlan {
+    static constexpr int PLANE_B = WMAX * TC_BK * 4;                  // one B plane
+    static constexpr int MMA_STAGE = 4 * TC_PLANE_A + 4 * PLANE_B;   // hi/lo x re/im planes of A and B
+    static constexpr int RAW_A = TC_BM * TC_BK * 8;                   // raw complex64 A stage (8 KB)
+    static constexpr int RAW_STAGE = RAW_A + WMAX * TC_BK * 8;
+    static constexpr int BUDGET = 113 * 1024 - 64;                    // two CTAs per SM
+    static constexpr int P_FIT = (BUDGET - 2 * MMA_STAGE) / RAW_STAGE;
+    static constexpr int P = P_FIT > 6 ? 6 : P_FIT;                   // raw stages in the ring
+    static constexpr int SMEM = 2 * MMA_STAGE + P * RAW_STAGE + 64;   // + mbarriers, TMEM slot, job
+    static_assert(P >= 3, "raw ring too shallow");
+};
 
 __device__ int g_tc_status = 0;
 
@@ -158,14 +170,36 @@ __device__ __forceinline__ void put4(unsigned char *planes, int plane_bytes, uin
     *reinterpret_cast<float4 *>(planes + 3 * plane_bytes + off) = make_float4(il[0], il[1], il[2], il[3]);
 }
 
+// Complex element (row, l) of a raw A stage, l < 8, as a complex64 index: the four k of a
+// (row, q = l / 4) unit sit in two 16-byte halves h = (l / 2) % 2, and unit u is the thread
+// index that converts it, so each half is read by the warp as one contiguous 512-byte run.
+__device__ __forceinline__ int raw_index(int row, int l, int units) {
+    const int q = l >> 2, h = (l >> 1) & 1, e = l & 1;
+    const int u = (((row >> 3) << 1) + q) * 8 + (row & 7);
+    return h * 2 * units + u * 2 + e;
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int WMAX>
 __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
+    using PL = TcPlan<WMAX>;
+    constexpr int P = PL::P;
     const int z = blockIdx.z;
     const int tile = blockIdx.x;
     if (tile >= g.ntiles[z]) return;
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + TC_NSTAGE * TC_STAGE);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + TC_NSTAGE * TC_STAGE + 8 * TC_NSTAGE);
-    int *s_job = reinterpret_cast<int *>(smem + TC_NSTAGE * TC_STAGE + 8 * TC_NSTAGE + 4);
+    unsigned char *raw = smem + 2 * PL::MMA_STAGE;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(raw + P * PL::RAW_STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(raw + P * PL::RAW_STAGE + 16);
+    int *s_job = reinterpret_cast<int *>(raw + P * PL::RAW_STAGE + 20);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GJob *jobs = g.jobs[z];
     if (tid == 0) {
@@ -184,7 +218,7 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
     const GJob J = jobs[*s_job];
     int t = tile - J.tile0;
     const int ntn = (J.n + TC_BN - 1) / TC_BN;
-    const int w = ((J.n + ntn - 1) / ntn + 15) / 16 * 16;     // tile width, <= 128
+    const int w = ((J.n + ntn - 1) / ntn + 15) / 16 * 16;     // tile width, <= WMAX (checked at planning)
     const int tmn = J.tm * ntn;
     const int kslice = t / tmn;
     t -= kslice * tmn;
@@ -205,6 +239,7 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
     }
 
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t rbase = (uint32_t)__cvta_generic_to_shared(raw);
     const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(mbar);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -214,8 +249,7 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int b = 0; b < TC_NSTAGE; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8 * b) : "memory");
+        for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8 * b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before_sync();
@@ -226,61 +260,84 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
     const c64 *__restrict__ A = g.A[z] + J.a;
     const c64 *__restrict__ B = g.B[z] + J.b;
     const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
-    // Staging unit of a thread: 4 consecutive kk (q = 0 or 1) of one row of A and one row
-    // of B (as N x K).  Along a unit-stride row index, the warp's lanes take consecutive
-    // rows (coalesced loads); along a unit-stride kk, 8 lanes take 8 consecutive rows of one
-    // q.  Either way each quarter-warp stores 128 contiguous bytes per plane.
-    int ia, qa, jb, qb;
-    if (J.acs == 1) { ia = 8 * (tid >> 4) + (tid & 7); qa = (tid >> 3) & 1; }
-    else { ia = tid & 127; qa = tid >> 7; }
-    if (J.brs == 1) { jb = 8 * (tid >> 4) + (tid & 7); qb = (tid >> 3) & 1; }
-    else { jb = tid & 127; qb = tid >> 7; }
-    const bool va = i0 + ia < J.m, vb = jb < w && j0 + jb < J.n;
-    const uint32_t oa = core_off(ia, qa), ob = core_off(jb, qb);
-    c64 ra[4], rb[4];
-    auto load = [&](int l0) {
+    // cp.async of one raw stage (k = l0 .. l0 + 7): 1024 A elements (4 per thread) and w x 8 B
+    // elements, mapped so that consecutive threads read consecutive addresses.
+    const bool a_rows = (J.ars == 1), b_cols = (J.bcs == 1);
+    auto issue = [&](int st, int slot) {
+        const int l0 = kbeg + TC_BK * st;
+        const uint32_t ra = rbase + slot * PL::RAW_STAGE, rb = ra + PL::RAW_A;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int l = l0 + 4 * qa + e;
-            c64 v = mk<float>(0, 0);
-            if (va && l < kend) v = A[(int64_t)(i0 + ia) * J.ars + (int64_t)l * J.acs];
-            ra[e] = conjA ? conj(v) : v;
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int row = a_rows ? (e & 127) : (e >> 3), l = a_rows ? (e >> 7) : (e & 7);
+            const bool v = (i0 + row < J.m) && (l0 + l < kend);
+            const c64 *src = v ? A + (int64_t)(i0 + row) * J.ars + (int64_t)(l0 + l) * J.acs : A;
+            cp_async8(ra + 8 * raw_index(row, l, TC_BM * 2), src, v);
         }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int l = l0 + 4 * qb + e;
-            c64 v = mk<float>(0, 0);
-            if (vb && l < kend) v = B[(int64_t)l * J.brs + (int64_t)(j0 + jb) * J.bcs];
-            rb[e] = conjB ? conj(v) : v;
+        for (int e = tid; e < w * TC_BK; e += 256) {
+            const int j = b_cols ? (e % w) : (e >> 3), l = b_cols ? (e / w) : (e & 7);
+            const bool v = (j0 + j < J.n) && (l0 + l < kend);
+            const c64 *src = v ? B + (int64_t)(l0 + l) * J.brs + (int64_t)(j0 + j) * J.bcs : B;
+            cp_async8(rb + 8 * raw_index(j, l, WMAX * 2), src, v);
         }
     };
-    auto store = [&](int buf) {
-        unsigned char *sa = smem + buf * TC_STAGE;
-        put4(sa, TC_PLANE_A, oa, ra);
-        if (jb < w) put4(sa + 4 * TC_PLANE_A, TC_PLANE_B, ob, rb);
+    // conversion unit of a thread: row r = 8 (tid / 16) + tid % 8, k-group q = (tid / 8) % 2 of
+    // A (and of B when r < w); its unit index is tid
+    const int ur = 8 * (tid >> 4) + (tid & 7), uq = (tid >> 3) & 1;
+    const uint32_t uoff = core_off(ur, uq);
+    auto convert = [&](int slot, int buf) {
+        const unsigned char *ra = raw + slot * PL::RAW_STAGE;
+        unsigned char *pa = smem + buf * PL::MMA_STAGE;
+        c64 v[4];
+        {
+            const float4 h0 = *reinterpret_cast<const float4 *>(ra + 16 * tid);
+            const float4 h1 = *reinterpret_cast<const float4 *>(ra + 16 * (TC_BM * 2) + 16 * tid);
+            v[0] = mk<float>(h0.x, h0.y); v[1] = mk<float>(h0.z, h0.w);
+            v[2] = mk<float>(h1.x, h1.y); v[3] = mk<float>(h1.z, h1.w);
+            if (conjA)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e].im = -v[e].im;
+            put4(pa, TC_PLANE_A, uoff, v);
+        }
+        if (ur < w) {
+            const unsigned char *rb = ra + PL::RAW_A;
+            const float4 h0 = *reinterpret_cast<const float4 *>(rb + 16 * tid);
+            const float4 h1 = *reinterpret_cast<const float4 *>(rb + 16 * (WMAX * 2) + 16 * tid);
+            v[0] = mk<float>(h0.x, h0.y); v[1] = mk<float>(h0.z, h0.w);
+            v[2] = mk<float>(h1.x, h1.y); v[3] = mk<float>(h1.z, h1.w);
+            if (conjB)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e].im = -v[e].im;
+            put4(pa + 4 * TC_PLANE_A, PL::PLANE_B, uoff, v);
+        }
     };
 
     // Cr = Ar Br - Ai Bi, Ci = Ar Bi + Ai Br on the (already conjugated) planes
     const uint32_t id_pos = instr_desc(w, false), id_neg = instr_desc(w, true);
     const uint32_t t_re = tmem, t_im = tmem + 128;
     bool ok = true;
-    // Step s: the MMAs of stage s (buffer s % 3); then, once the MMAs of stage s - 2 have
-    // released buffer (s + 1) % 3, stage s + 1 is stored from registers and the loads of
-    // stage s + 2 are issued.
-    load(kbeg);
-    store(0);
-    if (nst > 1) load(kbeg + TC_BK);
+    // prologue: P - 1 raw stages in flight (one commit group each, empty groups past the end)
+    for (int p = 0; p < P - 1; ++p) {
+        if (p < nst) issue(p, p);
+        cp_async_commit();
+    }
     for (int s = 0; s < nst; ++s) {
+        cp_async_wait<P - 2>();                     // raw stage s has landed (this thread's copies)
+        __syncthreads();                            // ... everybody's; stage s - 1 is converted
+        if (s + P - 1 < nst) issue(s + P - 1, (s + P - 1) % P);
+        cp_async_commit();
+        const int buf = s & 1;
+        if (s >= 2 && ok && !mbar_wait(mb0 + 8 * buf, ((s - 2) >> 1) & 1)) ok = false;   // MMAs of s - 2
+        convert(s % P, buf);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        const int buf = s % TC_NSTAGE;
         if (tid == 0) {
             fence_after_sync();
-            const uint32_t sa = sbase + buf * TC_STAGE, sb = sa + 4 * TC_PLANE_A;
+            const uint32_t sa = sbase + buf * PL::MMA_STAGE, sb = sa + 4 * TC_PLANE_A;
             const uint64_t a0 = smem_desc(sa), a1 = smem_desc(sa + TC_PLANE_A), a2 = smem_desc(sa + 2 * TC_PLANE_A),
                            a3 = smem_desc(sa + 3 * TC_PLANE_A);
-            const uint64_t b0 = smem_desc(sb), b1 = smem_desc(sb + TC_PLANE_B), b2 = smem_desc(sb + 2 * TC_PLANE_B),
-                           b3 = smem_desc(sb + 3 * TC_PLANE_B);
+            const uint64_t b0 = smem_desc(sb), b1 = smem_desc(sb + PL::PLANE_B), b2 = smem_desc(sb + 2 * PL::PLANE_B),
+                           b3 = smem_desc(sb + 3 * PL::PLANE_B);
             const uint32_t first = (s == 0) ? 0u : 1u;
             mma_tf32(t_re, a0, b0, id_pos, first);      // Ar Br
             mma_tf32(t_re, a0, b1, id_pos, 1u);
@@ -296,16 +353,11 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
             mma_tf32(t_im, a3, b0, id_pos, 1u);
             mma_commit(mb0 + 8 * buf);
         }
-        if (s + 1 < nst) {
-            const int p = s - 2;                        // last stage that used buffer (s + 1) % 3
-            if (ok && p >= 0 && !mbar_wait(mb0 + 8 * (p % TC_NSTAGE), (p / TC_NSTAGE) & 1)) ok = false;
-            store((s + 1) % TC_NSTAGE);
-            if (s + 2 < nst) load(kbeg + TC_BK * (s + 2));
-        }
     }
+    cp_async_wait<0>();
     {
         const int p = nst - 1;                          // its commit covers every earlier MMA
-        if (ok && !mbar_wait(mb0 + 8 * (p % TC_NSTAGE), (p / TC_NSTAGE) & 1)) ok = false;
+        if (ok && !mbar_wait(mb0 + 8 * (p & 1), (p >> 1) & 1)) ok = false;
     }
     fence_after_sync();
     ok = __syncthreads_and(ok);
@@ -351,15 +403,25 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
 
 }  // namespace
 
-void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st) {
-    static int attr_dev = -1;
+template <int WMAX> void launch_tc_w(const GemmArgs<float> &g, dim3 grid, cudaStream_t st) {
+    static bool attr_set[64] = {};                  // per device: the kernel's shared-memory opt-in
     int dev = 0;
     cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-        attr_dev = dev;
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        cudaFuncSetAttribute(k_gemm_tc<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcPlan<WMAX>::SMEM);
+        attr_set[dev] = true;
     }
-    k_gemm_tc<<<grid, 256, TC_SMEM, st>>>(g);
+    k_gemm_tc<WMAX><<<grid, 256, TcPlan<WMAX>::SMEM, st>>>(g);
+}
+
+void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st) {
+    const int wm = g.wmax > 0 ? g.wmax : 128;      // unplanned launches take the widest plan
+    if (wm <= 32)
+        launch_tc_w<32>(g, grid, st);
+    else if (wm <= 64)
+        launch_tc_w<64>(g, grid, st);
+    else
+        launch_tc_w<128>(g, grid, st);
 }
 
 int gemm_tc_status(bool reset) {

@@ -638,7 +638,15 @@ __global__ void __launch_bounds__(256) k_refine_resid(DevCSR A, DevCSR M, ResidA
         const c128 *X = r.Xz[z];
         for (int c = lane; c < r.k; c += 32) {
             c128 ax = mk<double>(0, 0);
-            for (int64_t p = ab; p < ae; ++p) fma_acc(ax, A.v[p], X[(int64_t)A.ci[p] * r.ldx + c]);
+            if (A.vr) {                                  // real matrix: 2 FMAs per entry instead of 4
+                for (int64_t p = ab; p < ae; ++p) {
+                    const c128 x = X[(int64_t)A.ci[p] * r.ldx + c];
+                    ax.re = fma(A.vr[p], x.re, ax.re);
+                    ax.im = fma(A.vr[p], x.im, ax.im);
+                }
+            } else {
+                for (int64_t p = ab; p < ae; ++p) fma_acc(ax, A.v[p], X[(int64_t)A.ci[p] * r.ldx + c]);
+            }
             double mr = 0.0, mi = 0.0;
             c128 mx = mk<double>(0, 0);
             if (M.vr) {
@@ -809,16 +817,40 @@ void launch_lincomb(const LinArgs &a, cudaStream_t st) {
 }
 
 // ============================================================== column norms
-// stage 1: CTA b sums rows b, b + G, b + 2G, ... into part[b * k + c];  stage 2: one warp
-// per column adds the COLNORM_PARTS partial sums (fixed order: deterministic).
+// stage 1: CTA b sums a contiguous chunk of rows into part[b * k + c]: for k <= 256 the
+// threads form 256 / k row groups of k consecutive columns, so a warp reads consecutive
+// addresses of a row-major block; the groups' sums are added in a fixed order through shared
+// memory.  stage 2: one warp per column adds the COLNORM_PARTS partial sums (fixed order:
+// deterministic).
 __global__ void __launch_bounds__(256) k_colnorm_part(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx,
                                                       double *__restrict__ part, int imag_only) {
+    __shared__ double red[256];
+    const int64_t rpc = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = r0 + rpc < n ? r0 + rpc : n;
+    if (k <= 256) {
+        const int rpp = 256 / k, c = threadIdx.x % k, rr = threadIdx.x / k;
+        double s = 0.0;
+        if (rr < rpp) {
+            if (imag_only)
+                for (int64_t i = r0 + rr; i < r1; i += rpp) s = fma(X[i * ldx + c].im, X[i * ldx + c].im, s);
+            else
+                for (int64_t i = r0 + rr; i < r1; i += rpp) s += abs2(X[i * ldx + c]);
+        }
+        red[threadIdx.x] = s;
+        __syncthreads();
+        if (threadIdx.x < k) {
+            double t = 0.0;
+            for (int q = 0; q < rpp; ++q) t += red[q * k + threadIdx.x];
+            part[(int64_t)blockIdx.x * k + threadIdx.x] = t;
+        }
+        return;
+    }
     for (int c = threadIdx.x; c < k; c += 256) {
         double s = 0.0;
         if (imag_only)
-            for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s = fma(X[i * ldx + c].im, X[i * ldx + c].im, s);
+            for (int64_t i = r0; i < r1; ++i) s = fma(X[i * ldx + c].im, X[i * ldx + c].im, s);
         else
-            for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s += abs2(X[i * ldx + c]);
+            for (int64_t i = r0; i < r1; ++i) s += abs2(X[i * ldx + c]);
         part[(int64_t)blockIdx.x * k + c] = s;
     }
 }

@@ -8,6 +8,7 @@ template <class T> struct GemmArgs {
     int bm;                              // tile height of this launch (64, or 128 for complex64)
     int bn;                              // tile width: 64 or 128 (bm = bn = 128: complex64 tensor cores)
     int real;                            // complex128 launches: all operands real (one FMA per product)
+    int wmax;                            // tensor-core launches: widest C tile of any job (<= 128)
     const GJob *jobs[MAX_INST];
     const int32_t *tmap[MAX_INST];       // job of every tile of the launch, or null (binary search)
     int njobs[MAX_INST];

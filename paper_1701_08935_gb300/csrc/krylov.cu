@@ -55,18 +55,56 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
 // ones.  The partial sums are reduced in FP64 by k_multidot_sum.
 __global__ void __launch_bounds__(256) k_multidot(int64_t n, int k, const float2 *const *__restrict__ V, int j0, int nj,
                                                   const c128 *__restrict__ W, double2 *__restrict__ part) {
+    // rows in one contiguous chunk per CTA; for k <= 256 the threads form 256 / k row groups
+    // of k consecutive columns (consecutive addresses of the row-major blocks), and the
+    // groups' sums are added in a fixed order through shared memory
+    __shared__ float2 red[JT][256];
+    const int64_t rpc = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = r0 + rpc < n ? r0 + rpc : n;
+    if (k <= 256) {
+        const int rpp = 256 / k, c = threadIdx.x % k, rr = threadIdx.x / k;
+        float ar[JT], ai[JT];
+#pragma unroll
+        for (int t = 0; t < JT; ++t) ar[t] = ai[t] = 0.f;
+        if (rr < rpp)
+            for (int64_t i = r0 + rr; i < r1; i += rpp) {
+                const c128 w = W[i * k + c];
+                const float wr = f64_to_f32_trunc(w.re), wi = f64_to_f32_trunc(w.im);
+#pragma unroll
+                for (int t = 0; t < JT; ++t)
+                    if (t < nj) {
+                        const float2 v = V[j0 + t][i * k + c];
+                        ar[t] = fmaf(v.x, wr, fmaf(v.y, wi, ar[t]));        // conj(v) w
+                        ai[t] = fmaf(v.x, wi, fmaf(-v.y, wr, ai[t]));
+                    }
+            }
+#pragma unroll
+        for (int t = 0; t < JT; ++t) red[t][threadIdx.x] = make_float2(ar[t], ai[t]);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nj * k; e += 256) {
+            const int t = e / k, cc = e - t * k;
+            double sr = 0.0, si = 0.0;
+            for (int q = 0; q < rpp; ++q) {
+                const float2 v = red[t][q * k + cc];
+                sr += v.x;
+                si += v.y;
+            }
+            part[((int64_t)blockIdx.x * nj + t) * k + cc] = make_double2(sr, si);
+        }
+        return;
+    }
     for (int c = threadIdx.x; c < k; c += 256) {
         float ar[JT], ai[JT];
 #pragma unroll
         for (int t = 0; t < JT; ++t) ar[t] = ai[t] = 0.f;
-        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        for (int64_t i = r0; i < r1; ++i) {
             const c128 w = W[i * k + c];
             const float wr = f64_to_f32_trunc(w.re), wi = f64_to_f32_trunc(w.im);
 #pragma unroll
             for (int t = 0; t < JT; ++t)
                 if (t < nj) {
                     const float2 v = V[j0 + t][i * k + c];
-                    ar[t] = fmaf(v.x, wr, fmaf(v.y, wi, ar[t]));        // conj(v) w
+                    ar[t] = fmaf(v.x, wr, fmaf(v.y, wi, ar[t]));
                     ai[t] = fmaf(v.x, wi, fmaf(-v.y, wr, ai[t]));
                 }
         }
