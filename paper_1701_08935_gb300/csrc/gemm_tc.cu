@@ -8,30 +8,32 @@
 // Arithmetic: every complex64 operand x is split into two TF32 numbers, x = hi + lo with
 // hi = x rounded to 11 significant bits and lo = (x - hi) rounded the same way (3xTF32:
 // the products hi*hi + hi*lo + lo*hi are accumulated in FP32 in tensor memory, the
-// lo*lo term, at most 2^-24 of the product, is dropped).  A complex product takes four
-// real products, so one k-step of 8 issues 12 MMAs of 128 x w x 8:
-//      Cr += Ar Br - Ai Bi,  Ci += Ar Bi + Ai Br        (each real product: 3 MMAs)
-// with the minus taken by the instruction descriptor's negate-A bit (conjugated operands
-// are conjugated while they are staged).  The tensor core's FP32 accumulation truncates, so
-// products are ~5-10x less accurate than with FP32 FMAs (~1e-6 relative at k = 64); the FP64
-// refinement of every mixed-precision solve absorbs this (the same number of refinement
-// steps was measured either way).
+// lo*lo term, at most 2^-24 of the product, is dropped).  The real and imaginary parts of a
+// w-column C tile sit side by side in one 2w-column accumulator D = [Cr | Ci], and the B
+// operand is staged as four 2w-row planes
+//      B0 = [Br_hi ; Bi_hi], B1 = [Br_lo ; Bi_lo], B2 = [-Bi_hi ; Br_hi], B3 = [-Bi_lo ; Br_lo],
+// so one k-step of 8 is six MMAs of 128 x 2w x 8:
+//      D += Ar_hi B0 + Ar_hi B1 + Ar_lo B0 + Ai_hi B2 + Ai_hi B3 + Ai_lo B2,
+// which gives Cr = Ar Br - Ai Bi and Ci = Ar Bi + Ai Br (conjugated operands are conjugated
+// while they are staged).  The tensor core's FP32 accumulation truncates, so products are
+// ~5-10x less accurate than with FP32 FMAs (~1e-6 relative at k = 64); the FP64 refinement of
+// every mixed-precision solve absorbs this.
 //
 // Tiles: one CTA per 128 x w tile of C, w <= 128 columns chosen per job so that the
-// ceil(n / 128) column tiles have equal width (a multiple of 16).  Two CTAs share an SM;
-// each allocates 256 tensor-memory columns (Cr in [0, 128), Ci in [128, 256)).
+// ceil(n / 128) column tiles have equal width (a multiple of 16); 256 tensor-memory columns
+// per CTA.
 //
-// Pipeline: the operands stream through a ring of P raw stages (k = 8 complex each) filled
-// by cp.async (8-byte copies with zero fill at the edges, so no thread waits on a global
-// load); P - 1 stages are in flight while one is converted.  Each step converts the oldest
-// raw stage (conjugation, hi/lo split) into one of two MMA stages in the canonical
-// no-swizzle K-major layout, and one elected thread issues that stage's MMAs and commits
-// them to its mbarrier; an MMA stage is overwritten once the MMAs that read it (two steps
-// earlier) have completed.  P depends on the widest tile of the launch (WMAX = 32, 64, 128:
-// P = 6, 5, 3) so that two CTAs fit an SM's shared memory.  Every wait on an mbarrier is
-// bounded in time (2 s): on expiry the CTA skips its remaining waits and its epilogue,
-// records ZOLO_ETIMEOUT in a device status word (read by gemm_tc_status) and releases its
-// tensor memory.
+// Pipeline (warp-specialised): eight converter warps stream the operands through a ring of
+// P raw stages (k = 8 complex each) filled by cp.async (8-byte copies with zero fill at the
+// edges), P - 1 stages in flight; each converts the oldest raw stage (conjugation, hi/lo
+// split) into one of NB MMA stages in the canonical no-swizzle K-major layout and arrives on
+// that stage's "full" mbarrier.  A ninth warp issues each stage's six MMAs once it is full and
+// commits them to the stage's "empty" mbarrier, which the converters wait on before they
+// overwrite it, so the MMA issue never holds up the conversion.  The plan depends on the
+// widest tile of the launch: WMAX = 32 and 64 run two CTAs per SM (NB = 3 and 2), WMAX = 128
+// one (NB = 3).  Every wait on an mbarrier is bounded in time (2 s): on expiry the thread skips
+// its remaining waits, the CTA skips its epilogue, records ZOLO_ETIMEOUT in a device status
+// word (read by gemm_tc_status) and releases its tensor memory.
 #include "kernels.cuh"
 #include "zolo.h"
 
@@ -50,16 +52,18 @@ constexpr uint64_t TC_WAIT_NS = 2000000000ull;              // 2 s per mbarrier 
 
 // Shared-memory plan of a launch whose tiles are at most WMAX wide.
 template <int WMAX> struct TcPlan {
-    static constexpr int PLANE_B = WMAX * TC_BK * 4;                  // one B plane
-    static constexpr int MMA_STAGE = 4 * TC_PLANE_A + 4 * PLANE_B;   // hi/lo x re/im planes of A and B
+    static constexpr int PLANE_B2 = 2 * WMAX * TC_BK * 4;             // one 2w-row B plane
+    static constexpr int MMA_STAGE = 4 * TC_PLANE_A + 4 * PLANE_B2;   // A and B planes of a k-step
     static constexpr int RAW_A = TC_BM * TC_BK * 8;                   // raw complex64 A stage (8 KB)
     static constexpr int RAW_STAGE = RAW_A + WMAX * TC_BK * 8;
-    static constexpr int BUDGET = 113 * 1024 - 64;                    // two CTAs per SM
-    static constexpr int P_FIT = (BUDGET - 2 * MMA_STAGE) / RAW_STAGE;
-    static constexpr int P = P_FIT > 6 ? 6 : P_FIT;                   // raw stages in the ring
-    static constexpr int SMEM = 2 * MMA_STAGE + P * RAW_STAGE + 64;   // + mbarriers, TMEM slot, job
-    static_assert(P >= 3, "raw ring too shallow");
+    static constexpr int CTAS = WMAX <= 64 ? 2 : 1;                   // CTAs per SM
+    static constexpr int NB = WMAX <= 32 ? 3 : (WMAX <= 64 ? 2 : 3);  // MMA stages
+    static constexpr int P = 4;                                       // raw stages in the ring
+    static constexpr int BAR = 128;                                   // mbarriers, TMEM slot, job
+    static constexpr int SMEM = NB * MMA_STAGE + P * RAW_STAGE + BAR;
+    static_assert(SMEM * CTAS + 1024 * CTAS <= 233472, "shared memory plan too large");
 };
+constexpr int TC_THREADS = 288;              // 8 converter warps + 1 MMA warp
 
 __device__ int g_tc_status = 0;
 
@@ -129,22 +133,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// 32 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // x rounded to TF32 (11 significant bits), ties away from zero, with two integer
@@ -188,18 +188,48 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void converters_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Split four complex B values (row j of the w-row tile, one k-group) into the four 2w-row
+// planes B0 = [Br_hi ; Bi_hi], B1 = [Br_lo ; Bi_lo], B2 = [-Bi_hi ; Br_hi], B3 = [-Bi_lo ; Br_lo].
+__device__ __forceinline__ void put4_b(unsigned char *planes, int plane_bytes, uint32_t off_top, uint32_t off_bot,
+                                       const c64 *v) {
+    float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        rh[e] = tf32_round(v[e].re);
+        rl[e] = tf32_round(v[e].re - rh[e]);
+        ih[e] = tf32_round(v[e].im);
+        il[e] = tf32_round(v[e].im - ih[e]);
+    }
+    unsigned char *p0 = planes, *p1 = planes + plane_bytes, *p2 = planes + 2 * plane_bytes,
+                  *p3 = planes + 3 * plane_bytes;
+    *reinterpret_cast<float4 *>(p0 + off_top) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+    *reinterpret_cast<float4 *>(p0 + off_bot) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+    *reinterpret_cast<float4 *>(p1 + off_top) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+    *reinterpret_cast<float4 *>(p1 + off_bot) = make_float4(il[0], il[1], il[2], il[3]);
+    *reinterpret_cast<float4 *>(p2 + off_top) = make_float4(-ih[0], -ih[1], -ih[2], -ih[3]);
+    *reinterpret_cast<float4 *>(p2 + off_bot) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+    *reinterpret_cast<float4 *>(p3 + off_top) = make_float4(-il[0], -il[1], -il[2], -il[3]);
+    *reinterpret_cast<float4 *>(p3 + off_bot) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+}
+
 template <int WMAX>
-__global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
+__global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(GemmArgs<float> g) {
     using PL = TcPlan<WMAX>;
-    constexpr int P = PL::P;
+    constexpr int P = PL::P, NB = PL::NB;
     const int z = blockIdx.z;
     const int tile = blockIdx.x;
     if (tile >= g.ntiles[z]) return;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *raw = smem + 2 * PL::MMA_STAGE;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(raw + P * PL::RAW_STAGE);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(raw + P * PL::RAW_STAGE + 16);
-    int *s_job = reinterpret_cast<int *>(raw + P * PL::RAW_STAGE + 20);
+    unsigned char *raw = smem + NB * PL::MMA_STAGE;
+    unsigned char *ctl = raw + P * PL::RAW_STAGE;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(ctl);                 // full[0..NB), empty[0..NB)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ctl + 16 * NB);
+    int *s_job = reinterpret_cast<int *>(ctl + 16 * NB + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GJob *jobs = g.jobs[z];
     if (tid == 0) {
@@ -231,7 +261,7 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
     const bool sub = J.flags & GJ_SUB, add = J.flags & GJ_ACC, atom = J.ks > 1;
     if (nst == 0) {                       // empty k-slice: only a plain product writes (zeros)
         if (!(sub || add || atom))
-            for (int e = tid; e < TC_BM * w; e += 256) {
+            for (int e = tid; e < TC_BM * w; e += TC_THREADS) {
                 const int i = i0 + e / w, j = j0 + e % w;
                 if (i < J.m && j < J.n) C[(int64_t)i * J.crs + (int64_t)j * J.ccs] = mk<float>(0, 0);
             }
@@ -240,7 +270,7 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
 
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t rbase = (uint32_t)__cvta_generic_to_shared(raw);
-    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(mbar);
+    const uint32_t mfull = (uint32_t)__cvta_generic_to_shared(mbar), mempty = mfull + 8 * NB;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(tmem_slot)),
@@ -249,149 +279,153 @@ __global__ void __launch_bounds__(256, 2) k_gemm_tc(GemmArgs<float> g) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8 * b) : "memory");
+        for (int b = 0; b < NB; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" ::"r"(mfull + 8 * b) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mempty + 8 * b) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-
-    const c64 *__restrict__ A = g.A[z] + J.a;
-    const c64 *__restrict__ B = g.B[z] + J.b;
-    const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
-    // cp.async of one raw stage (k = l0 .. l0 + 7): 1024 A elements (4 per thread) and w x 8 B
-    // elements, mapped so that consecutive threads read consecutive addresses.
-    const bool a_rows = (J.ars == 1), b_cols = (J.bcs == 1);
-    auto issue = [&](int st, int slot) {
-        const int l0 = kbeg + TC_BK * st;
-        const uint32_t ra = rbase + slot * PL::RAW_STAGE, rb = ra + PL::RAW_A;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = tid + 256 * q;
-            const int row = a_rows ? (e & 127) : (e >> 3), l = a_rows ? (e >> 7) : (e & 7);
-            const bool v = (i0 + row < J.m) && (l0 + l < kend);
-            const c64 *src = v ? A + (int64_t)(i0 + row) * J.ars + (int64_t)(l0 + l) * J.acs : A;
-            cp_async8(ra + 8 * raw_index(row, l, TC_BM * 2), src, v);
-        }
-        for (int e = tid; e < w * TC_BK; e += 256) {
-            const int j = b_cols ? (e % w) : (e >> 3), l = b_cols ? (e / w) : (e & 7);
-            const bool v = (j0 + j < J.n) && (l0 + l < kend);
-            const c64 *src = v ? B + (int64_t)(l0 + l) * J.brs + (int64_t)(j0 + j) * J.bcs : B;
-            cp_async8(rb + 8 * raw_index(j, l, WMAX * 2), src, v);
-        }
-    };
-    // conversion unit of a thread: row r = 8 (tid / 16) + tid % 8, k-group q = (tid / 8) % 2 of
-    // A (and of B when r < w); its unit index is tid
-    const int ur = 8 * (tid >> 4) + (tid & 7), uq = (tid >> 3) & 1;
-    const uint32_t uoff = core_off(ur, uq);
-    auto convert = [&](int slot, int buf) {
-        const unsigned char *ra = raw + slot * PL::RAW_STAGE;
-        unsigned char *pa = smem + buf * PL::MMA_STAGE;
-        c64 v[4];
-        {
-            const float4 h0 = *reinterpret_cast<const float4 *>(ra + 16 * tid);
-            const float4 h1 = *reinterpret_cast<const float4 *>(ra + 16 * (TC_BM * 2) + 16 * tid);
-            v[0] = mk<float>(h0.x, h0.y); v[1] = mk<float>(h0.z, h0.w);
-            v[2] = mk<float>(h1.x, h1.y); v[3] = mk<float>(h1.z, h1.w);
-            if (conjA)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v[e].im = -v[e].im;
-            put4(pa, TC_PLANE_A, uoff, v);
-        }
-        if (ur < w) {
-            const unsigned char *rb = ra + PL::RAW_A;
-            const float4 h0 = *reinterpret_cast<const float4 *>(rb + 16 * tid);
-            const float4 h1 = *reinterpret_cast<const float4 *>(rb + 16 * (WMAX * 2) + 16 * tid);
-            v[0] = mk<float>(h0.x, h0.y); v[1] = mk<float>(h0.z, h0.w);
-            v[2] = mk<float>(h1.x, h1.y); v[3] = mk<float>(h1.z, h1.w);
-            if (conjB)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v[e].im = -v[e].im;
-            put4(pa + 4 * TC_PLANE_A, PL::PLANE_B, uoff, v);
-        }
-    };
-
-    // Cr = Ar Br - Ai Bi, Ci = Ar Bi + Ai Br on the (already conjugated) planes
-    const uint32_t id_pos = instr_desc(w, false), id_neg = instr_desc(w, true);
-    const uint32_t t_re = tmem, t_im = tmem + 128;
     bool ok = true;
-    // prologue: P - 1 raw stages in flight (one commit group each, empty groups past the end)
-    for (int p = 0; p < P - 1; ++p) {
-        if (p < nst) issue(p, p);
-        cp_async_commit();
-    }
-    for (int s = 0; s < nst; ++s) {
-        cp_async_wait<P - 2>();                     // raw stage s has landed (this thread's copies)
-        __syncthreads();                            // ... everybody's; stage s - 1 is converted
-        if (s + P - 1 < nst) issue(s + P - 1, (s + P - 1) % P);
-        cp_async_commit();
-        const int buf = s & 1;
-        if (s >= 2 && ok && !mbar_wait(mb0 + 8 * buf, ((s - 2) >> 1) & 1)) ok = false;   // MMAs of s - 2
-        convert(s % P, buf);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            fence_after_sync();
-            const uint32_t sa = sbase + buf * PL::MMA_STAGE, sb = sa + 4 * TC_PLANE_A;
-            const uint64_t a0 = smem_desc(sa), a1 = smem_desc(sa + TC_PLANE_A), a2 = smem_desc(sa + 2 * TC_PLANE_A),
-                           a3 = smem_desc(sa + 3 * TC_PLANE_A);
-            const uint64_t b0 = smem_desc(sb), b1 = smem_desc(sb + PL::PLANE_B), b2 = smem_desc(sb + 2 * PL::PLANE_B),
-                           b3 = smem_desc(sb + 3 * PL::PLANE_B);
-            const uint32_t first = (s == 0) ? 0u : 1u;
-            mma_tf32(t_re, a0, b0, id_pos, first);      // Ar Br
-            mma_tf32(t_re, a0, b1, id_pos, 1u);
-            mma_tf32(t_re, a1, b0, id_pos, 1u);
-            mma_tf32(t_re, a2, b2, id_neg, 1u);         // - Ai Bi
-            mma_tf32(t_re, a2, b3, id_neg, 1u);
-            mma_tf32(t_re, a3, b2, id_neg, 1u);
-            mma_tf32(t_im, a0, b2, id_pos, first);      // Ar Bi
-            mma_tf32(t_im, a0, b3, id_pos, 1u);
-            mma_tf32(t_im, a1, b2, id_pos, 1u);
-            mma_tf32(t_im, a2, b0, id_pos, 1u);         // Ai Br
-            mma_tf32(t_im, a2, b1, id_pos, 1u);
-            mma_tf32(t_im, a3, b0, id_pos, 1u);
-            mma_commit(mb0 + 8 * buf);
+
+    if (warp == 8) {
+        // ---- MMA warp: one thread issues every stage's six MMAs once the stage is full
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(2 * w, false);
+            for (int s = 0; s < nst && ok; ++s) {
+                const int buf = s % NB;
+                if (!mbar_wait(mfull + 8 * buf, (s / NB) & 1)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t sa = sbase + buf * PL::MMA_STAGE, sb = sa + 4 * TC_PLANE_A;
+                const uint64_t a0 = smem_desc(sa), a1 = smem_desc(sa + TC_PLANE_A),
+                               a2 = smem_desc(sa + 2 * TC_PLANE_A), a3 = smem_desc(sa + 3 * TC_PLANE_A);
+                const uint64_t b0 = smem_desc(sb), b1 = smem_desc(sb + PL::PLANE_B2),
+                               b2 = smem_desc(sb + 2 * PL::PLANE_B2), b3 = smem_desc(sb + 3 * PL::PLANE_B2);
+                mma_tf32(tmem, a0, b0, idesc, s > 0 ? 1u : 0u);    // Ar_hi [Br_hi | Bi_hi]
+                mma_tf32(tmem, a0, b1, idesc, 1u);                 // Ar_hi [Br_lo | Bi_lo]
+                mma_tf32(tmem, a1, b0, idesc, 1u);                 // Ar_lo [Br_hi | Bi_hi]
+                mma_tf32(tmem, a2, b2, idesc, 1u);                 // Ai_hi [-Bi_hi | Br_hi]
+                mma_tf32(tmem, a2, b3, idesc, 1u);                 // Ai_hi [-Bi_lo | Br_lo]
+                mma_tf32(tmem, a3, b2, idesc, 1u);                 // Ai_lo [-Bi_hi | Br_hi]
+                mma_commit(mempty + 8 * buf);
+            }
         }
+        __syncwarp();
+    } else {
+        // ---- converter warps
+        const c64 *__restrict__ A = g.A[z] + J.a;
+        const c64 *__restrict__ B = g.B[z] + J.b;
+        const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
+        // cp.async of one raw stage (k = l0 .. l0 + 7): 1024 A elements (4 per thread) and
+        // w x 8 B elements, mapped so that consecutive threads read consecutive addresses
+        const bool a_rows = (J.ars == 1), b_cols = (J.bcs == 1);
+        auto issue = [&](int st, int slot) {
+            const int l0 = kbeg + TC_BK * st;
+            const uint32_t ra = rbase + slot * PL::RAW_STAGE, rb = ra + PL::RAW_A;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q;
+                const int row = a_rows ? (e & 127) : (e >> 3), l = a_rows ? (e >> 7) : (e & 7);
+                const bool v = (i0 + row < J.m) && (l0 + l < kend);
+                const c64 *src = v ? A + (int64_t)(i0 + row) * J.ars + (int64_t)(l0 + l) * J.acs : A;
+                cp_async8(ra + 8 * raw_index(row, l, TC_BM * 2), src, v);
+            }
+            for (int e = tid; e < w * TC_BK; e += 256) {
+                const int j = b_cols ? (e % w) : (e >> 3), l = b_cols ? (e / w) : (e & 7);
+                const bool v = (j0 + j < J.n) && (l0 + l < kend);
+                const c64 *src = v ? B + (int64_t)(l0 + l) * J.brs + (int64_t)(j0 + j) * J.bcs : B;
+                cp_async8(rb + 8 * raw_index(j, l, WMAX * 2), src, v);
+            }
+        };
+        // conversion unit of a thread: row r = 8 (tid / 16) + tid % 8 and k-group q = (tid / 8) % 2
+        // of A (and of B when r < w); its raw unit index is tid
+        const int ur = 8 * (tid >> 4) + (tid & 7), uq = (tid >> 3) & 1;
+        const uint32_t uoff = core_off(ur, uq);
+        const uint32_t boff_bot = core_off(ur + w, uq);
+        auto convert = [&](int slot, int buf) {
+            const unsigned char *ra = raw + slot * PL::RAW_STAGE;
+            unsigned char *pa = smem + buf * PL::MMA_STAGE;
+            c64 v[4];
+            {
+                const float4 h0 = *reinterpret_cast<const float4 *>(ra + 16 * tid);
+                const float4 h1 = *reinterpret_cast<const float4 *>(ra + 16 * (TC_BM * 2) + 16 * tid);
+                v[0] = mk<float>(h0.x, h0.y); v[1] = mk<float>(h0.z, h0.w);
+                v[2] = mk<float>(h1.x, h1.y); v[3] = mk<float>(h1.z, h1.w);
+                if (conjA)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[e].im = -v[e].im;
+                put4(pa, TC_PLANE_A, uoff, v);
+            }
+            if (ur < w) {
+                const unsigned char *rb = ra + PL::RAW_A;
+                const float4 h0 = *reinterpret_cast<const float4 *>(rb + 16 * tid);
+                const float4 h1 = *reinterpret_cast<const float4 *>(rb + 16 * (WMAX * 2) + 16 * tid);
+                v[0] = mk<float>(h0.x, h0.y); v[1] = mk<float>(h0.z, h0.w);
+                v[2] = mk<float>(h1.x, h1.y); v[3] = mk<float>(h1.z, h1.w);
+                if (conjB)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[e].im = -v[e].im;
+                put4_b(pa + 4 * TC_PLANE_A, PL::PLANE_B2, uoff, boff_bot, v);
+            }
+        };
+        for (int p = 0; p < P - 1; ++p) {           // prologue: P - 1 raw stages in flight
+            if (p < nst) issue(p, p);
+            cp_async_commit();
+        }
+        for (int s = 0; s < nst; ++s) {
+            cp_async_wait<P - 2>();                 // raw stage s has landed (this thread's copies)
+            converters_sync();                      // ... everybody's; stage s - 1 is converted
+            if (s + P - 1 < nst) issue(s + P - 1, (s + P - 1) % P);
+            cp_async_commit();
+            const int buf = s % NB;
+            if (s >= NB && ok && !mbar_wait(mempty + 8 * buf, ((s - NB) / NB) & 1)) ok = false;
+            convert(s % P, buf);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(mfull + 8 * buf);
+        }
+        cp_async_wait<0>();
+        const int p = nst - 1;                      // its commit covers every earlier MMA
+        if (ok && !mbar_wait(mempty + 8 * (p % NB), (p / NB) & 1)) ok = false;
+        fence_after_sync();
     }
-    cp_async_wait<0>();
-    {
-        const int p = nst - 1;                          // its commit covers every earlier MMA
-        if (ok && !mbar_wait(mb0 + 8 * (p & 1), (p >> 1) & 1)) ok = false;
-    }
-    fence_after_sync();
     ok = __syncthreads_and(ok);
 
-    if (ok) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (C rows), column chunks of 32
-        // alternating between warps w and w + 4
+    if (ok && warp < 8) {
+        // epilogue: warp v reads TMEM lanes 32 (v % 4) .. + 31 (C rows); column chunks of 16
+        // alternate between warps v and v + 4; Cr sits in columns [0, w), Ci in [w, 2w)
         const int qd = warp & 3, hf = warp >> 2;
         const int i = i0 + 32 * qd + lane;
-        const int nch = (w + 31) / 32;
+        const int nch = w / 16;
         for (int c = hf; c < nch; c += 2) {
-            float re[32], im[32];
-            const uint32_t ta = ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * c);
-            tmem_ld32(t_re + ta, re);
-            tmem_ld32(t_im + ta, im);
+            float re[16], im[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * c);
+            tmem_ld16(ta, re);
+            tmem_ld16(ta + (uint32_t)w, im);
             if (i < J.m) {
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                    const int jl = 32 * c + jj, j = j0 + jl;
-                    if (jl >= w || j >= J.n) continue;
-                    c64 *p = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int j = j0 + 16 * c + jj;
+                    if (j >= J.n) continue;
+                    c64 *q = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
                     const float vr = sub ? -re[jj] : re[jj], vi = sub ? -im[jj] : im[jj];
                     if (atom) {
-                        atomicAdd(reinterpret_cast<float2 *>(p), make_float2(vr, vi));
+                        atomicAdd(reinterpret_cast<float2 *>(q), make_float2(vr, vi));
                     } else if (sub || add) {
-                        const c64 o = *p;
-                        *p = mk<float>(o.re + vr, o.im + vi);
+                        const c64 o = *q;
+                        *q = mk<float>(o.re + vr, o.im + vi);
                     } else {
-                        *p = mk<float>(vr, vi);
+                        *q = mk<float>(vr, vi);
                     }
                 }
             }
         }
-    } else if (tid == 0) {
+    } else if (!ok && tid == 0) {
         atomicExch(&g_tc_status, ZOLO_ETIMEOUT);
     }
     fence_before_sync();
@@ -411,7 +445,7 @@ template <int WMAX> void launch_tc_w(const GemmArgs<float> &g, dim3 grid, cudaSt
         cudaFuncSetAttribute(k_gemm_tc<WMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcPlan<WMAX>::SMEM);
         attr_set[dev] = true;
     }
-    k_gemm_tc<WMAX><<<grid, 256, TcPlan<WMAX>::SMEM, st>>>(g);
+    k_gemm_tc<WMAX><<<grid, TC_THREADS, TcPlan<WMAX>::SMEM, st>>>(g);
 }
 
 void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st) {
