@@ -186,7 +186,9 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
     return L;
 }
 
-Launch add_rows(std::vector<RJob> &all, const std::vector<RJob> &jobs, int tile_rows) {
+// Append a launch of row jobs with tile_rows rows per CTA, or (square) 32 x 32 tiles of a
+// job's rows x rows block per CTA (matrix extend-add).
+Launch add_rows(std::vector<RJob> &all, const std::vector<RJob> &jobs, int tile_rows, bool square = false) {
     Launch L;
     L.off = (int64_t)all.size();
     int tiles = 0;
@@ -194,7 +196,7 @@ Launch add_rows(std::vector<RJob> &all, const std::vector<RJob> &jobs, int tile_
         if (j.rows <= 0) continue;
         j.tile0 = tiles;
         j.tr = (j.rows + tile_rows - 1) / tile_rows;
-        tiles += (tile_rows == 32) ? j.tr * j.tr : j.tr;   // 32: square extend-add tiles
+        tiles += square ? j.tr * j.tr : j.tr;
         all.push_back(j);
         L.cnt++;
     }
@@ -404,7 +406,7 @@ int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
                 if (nu == 0) continue;
                 jobs.push_back(rjob(h->f_off[c] + np + (int64_t)np * nf, h->f_off[p], h->f_rel[c], nu, nf, S.nf(p)));
             }
-            F.eadd.push_back(add_rows(ej, jobs, 32));
+            F.eadd.push_back(add_rows(ej, jobs, 32, true));
         }
         int maxnp = 0;
         for (int i = b; i < e; ++i) maxnp = std::max(maxnp, S.npiv[S.by_level[i]]);
@@ -448,7 +450,7 @@ int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
             stp.schur = add_gemm(gj, sc);
             F.steps.push_back(stp);
         }
-        // explicit pivot-block inverses L_pp^-1 and U_pp^-1 (row-major np x np), computed by
+        // explicit pivot-block inverses L_pp^-1 and U_pp^-1 (formed row-major np x np), computed by
         // blocked substitution against the identity with the diagonal-block inverses
         F.finv_lo = h->f_finv[s0];
         F.finv_hi = h->f_finv[s1] + 2 * (int64_t)S.npiv[s1] * S.npiv[s1];
@@ -459,6 +461,26 @@ int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
                 ey.push_back(rjob(0, h->f_finv[s], 0, S.npiv[s]));
             }
             F.eye = add_rows(ej, ey, 256);
+            // then transposed in place to column-major, so that the block solves stream them
+            // as contiguous columns (K^-1 and K^-H both)
+            Launch tp;
+            tp.off = (int64_t)ej.size();
+            int tiles = 0;
+            for (int i = b; i < e; ++i) {
+                const int sn = S.by_level[i];
+                const int np = S.npiv[sn];
+                if (np <= 0) continue;
+                for (int half = 0; half < 2; ++half) {
+                    RJob j = rjob(0, h->f_finv[sn] + (int64_t)half * np * np, 0, np);
+                    j.tr = (np + 31) / 32;
+                    j.tile0 = tiles;
+                    tiles += j.tr * (j.tr + 1) / 2;
+                    ej.push_back(j);
+                    tp.cnt++;
+                }
+            }
+            tp.ntiles = tiles;
+            F.tpose = tp;
         }
         for (int t = 0; t * NB < maxnp; ++t) {                      // L: forward, rows below
             std::vector<GJob> ap, up;
@@ -630,6 +652,13 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                 igemm(F.uinv[q], false);
                 igemm(F.uinv[q + 1], true);
             }
+            EyeArgs<T> tp;                                  // row-major -> column-major
+            std::memset(&tp, 0, sizeof(tp));
+            tp.jobs = h->d_ejobs + F.tpose.off;
+            tp.njobs = F.tpose.cnt;
+            tp.ntiles = F.tpose.ntiles;
+            for (int z = 0; z < ni; ++z) tp.P[z] = finv[z];
+            launch_transpose_sq<T>(tp, ni, st);
         }
     }
     return cuda_check(cudaGetLastError(), "factor launch");
@@ -714,7 +743,7 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
         }
         SOp og;
         og.kind = SOP_GATHER_IN;
-        og.L = add_rows(rj, g, ROWS_PER_TILE);
+        og.L = add_rows(rj, g, rows_per_tile(k));
         h->fwd.push_back(og);
         size_t maxkids = 0;
         for (int i = b; i < e; ++i) maxkids = std::max(maxkids, S.children[S.by_level[i]].size());
@@ -729,7 +758,7 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
             }
             SOp oe;
             oe.kind = SOP_EADD;
-            oe.L = add_rows(rj, ea, ROWS_PER_TILE);
+            oe.L = add_rows(rj, ea, rows_per_tile(k));
             h->fwd.push_back(oe);
         }
         std::vector<GJob> yN, yH, uN, uH;
@@ -739,8 +768,9 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
             const int64_t X = h->f_finv[s], o = h->f_off[s];
             const int64_t wp = h->f_wrow[s] * k, wu = (h->f_wrow[s] + np) * k, y = (int64_t)S.first[s] * k;
             // Y starts zeroed (the whole pivot-row block is cleared per solve): accumulate
-            yN.push_back(make_job(X, np, 1, wp, K, 1, y, K, 1, np, K, np, GJ_ACC));                     // Linv
-            yH.push_back(make_job(X + (int64_t)np * np, 1, np, wp, K, 1, y, K, 1, np, K, np,
+            // Linv and Uinv are stored column-major (transposed in place after they are formed)
+            yN.push_back(make_job(X, 1, np, wp, K, 1, y, K, 1, np, K, np, GJ_ACC));                     // Linv
+            yH.push_back(make_job(X + (int64_t)np * np, np, 1, wp, K, 1, y, K, 1, np, K, np,
                                   GJ_ACC | GJ_CONJA));                                                   // Uinv^H
             uN.push_back(make_job(o + np, 1, nf, y, K, 1, wu, K, 1, nu, K, np, GJ_SUB));                 // L_up
             uH.push_back(make_job(o + (int64_t)np * nf, nf, 1, y, K, 1, wu, K, 1, nu, K, np, GJ_SUB | GJ_CONJA));
@@ -761,24 +791,24 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
             aN.push_back(make_job(o + (int64_t)np * nf, 1, nf, wu, K, 1, y, K, 1, np, K, nu, GJ_SUB));  // U_pu
             aH.push_back(make_job(o + np, nf, 1, wu, K, 1, y, K, 1, np, K, nu, GJ_SUB | GJ_CONJA));      // L_up^H
             // W_p is cleared first (ROW_ZERO), then accumulated into
-            xN.push_back(make_job(X + (int64_t)np * np, np, 1, y, K, 1, wp, K, 1, np, K, np, GJ_ACC));   // Uinv
-            xH.push_back(make_job(X, 1, np, y, K, 1, wp, K, 1, np, K, np, GJ_ACC | GJ_CONJA));           // Linv^H
+            xN.push_back(make_job(X + (int64_t)np * np, 1, np, y, K, 1, wp, K, 1, np, K, np, GJ_ACC));   // Uinv
+            xH.push_back(make_job(X, np, 1, y, K, 1, wp, K, 1, np, K, np, GJ_ACC | GJ_CONJA));           // Linv^H
             sc.push_back(rjob(wp, 0, h->f_rows[s], np));
             zr.push_back(rjob(0, wp, 0, np));
         }
         SOp og;
         og.kind = SOP_GATHER_OUT;
-        og.L = add_rows(rj, g, ROWS_PER_TILE);
+        og.L = add_rows(rj, g, rows_per_tile(k));
         h->bwd.push_back(og);
         h->bwd.push_back(gemm_op(aN, aH, BK_POOL, BK_W, BK_YP));
         SOp oz;
         oz.kind = SOP_ZERO;
-        oz.L = add_rows(rj, zr, ROWS_PER_TILE);
+        oz.L = add_rows(rj, zr, rows_per_tile(k));
         h->bwd.push_back(oz);
         h->bwd.push_back(gemm_op(xN, xH, BK_INVFULL, BK_YP, BK_W));
         SOp os;
         os.kind = SOP_SCATTER_OUT;
-        os.L = add_rows(rj, sc, ROWS_PER_TILE);
+        os.L = add_rows(rj, sc, rows_per_tile(k));
         h->bwd.push_back(os);
     }
     // device copies: [GJob... | RJob...]
@@ -867,6 +897,7 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                 r.ntiles = o.L.ntiles;
                 r.map = (o.kind == SOP_EADD) ? h->d_rel : h->d_rows;
                 r.k = (int)k;
+                r.rpt = rows_per_tile(k);
                 r.ldw = k;
                 r.mode = (o.kind == SOP_EADD) ? ROW_EADD
                          : (o.kind == SOP_SCATTER_OUT ? ROW_SCATTER : (o.kind == SOP_ZERO ? ROW_ZERO : ROW_GATHER));

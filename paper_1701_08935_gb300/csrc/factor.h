@@ -28,6 +28,7 @@ struct FLevel {
     int64_t pool_lo = 0, pool_hi = 0;              // the level's fronts are contiguous
     int64_t finv_lo = 0, finv_hi = 0;              // ... and so are their pivot-block inverses
     Launch eye;                                     // identity start of those inverses
+    Launch tpose;                                   // their in-place transposes (row- to column-major)
     std::vector<Launch> linv, uinv;                // (apply, update) pairs per panel step
     int64_t asmA_lo = 0, asmA_hi = 0, asmB_lo = 0, asmB_hi = 0;
     std::vector<Launch> eadd;                      // one per child slot
@@ -74,7 +75,7 @@ struct zolo_factor_s {
     void *pool[ZOLO_MAX_R] = {};                   // per pole: fronts (T)
     void *inv[ZOLO_MAX_R] = {};                    // per pole: diagonal-block inverses (T)
     void *finv[ZOLO_MAX_R] = {};                   // per pole: full pivot-block inverses, L then U
-                                                   // (np x np each, row-major)
+                                                   // (np x np each, column-major once formed)
     int32_t *d_rows = nullptr, *d_rel = nullptr;
     int64_t *d_asm = nullptr;                      // [srcA | dstA | srcB | dstB]
     int64_t nA_asm = 0, nB_asm = 0;

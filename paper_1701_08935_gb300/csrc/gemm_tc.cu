@@ -30,8 +30,9 @@
 // that stage's "full" mbarrier.  A ninth warp issues each stage's six MMAs once it is full and
 // commits them to the stage's "empty" mbarrier, which the converters wait on before they
 // overwrite it, so the MMA issue never holds up the conversion.  The plan depends on the
-// widest tile of the launch: WMAX = 32 and 64 run two CTAs per SM (NB = 3 and 2), WMAX = 128
-// one (NB = 3).  Every wait on an mbarrier is bounded in time (2 s): on expiry the thread skips
+// widest tile of the launch (WMAX = 32, 64, 128: NB = 3, 2, 2 and P = 4, 4, 3), two CTAs per
+// SM; 128-wide tiles keep Cr and Ci in separate accumulators (twelve MMAs of N = w per
+// k-step) to fit.  Every wait on an mbarrier is bounded in time (2 s): on expiry the thread skips
 // its remaining waits, the CTA skips its epilogue, records ZOLO_ETIMEOUT in a device status
 // word (read by gemm_tc_status) and releases its tensor memory.
 #include "kernels.cuh"
@@ -52,13 +53,18 @@ constexpr uint64_t TC_WAIT_NS = 2000000000ull;              // 2 s per mbarrier 
 
 // Shared-memory plan of a launch whose tiles are at most WMAX wide.
 template <int WMAX> struct TcPlan {
-    static constexpr int PLANE_B2 = 2 * WMAX * TC_BK * 4;             // one 2w-row B plane
-    static constexpr int MMA_STAGE = 4 * TC_PLANE_A + 4 * PLANE_B2;   // A and B planes of a k-step
+    // FUSED: [Cr | Ci] in one 2w-column accumulator, six MMAs of N = 2w per k-step (B staged
+    // as 2w-row planes); otherwise Cr and Ci in separate 128-column accumulators, twelve MMAs
+    // of N = w (w-row B planes, -Ai Bi through the instruction's negate-A bit), which keeps
+    // the 128-wide tiles of the factorisation at two CTAs per SM
+    static constexpr bool FUSED = WMAX <= 64;
+    static constexpr int PLANE_B = (FUSED ? 2 : 1) * WMAX * TC_BK * 4;
+    static constexpr int MMA_STAGE = 4 * TC_PLANE_A + 4 * PLANE_B;   // A and B planes of a k-step
     static constexpr int RAW_A = TC_BM * TC_BK * 8;                   // raw complex64 A stage (8 KB)
     static constexpr int RAW_STAGE = RAW_A + WMAX * TC_BK * 8;
-    static constexpr int CTAS = WMAX <= 64 ? 2 : 1;                   // CTAs per SM
-    static constexpr int NB = WMAX <= 32 ? 3 : (WMAX <= 64 ? 2 : 3);  // MMA stages
-    static constexpr int P = 4;                                       // raw stages in the ring
+    static constexpr int CTAS = 2;                                    // CTAs per SM
+    static constexpr int NB = WMAX <= 32 ? 3 : 2;                     // MMA stages
+    static constexpr int P = WMAX <= 64 ? 4 : 3;                      // raw stages in the ring
     static constexpr int BAR = 128;                                   // mbarriers, TMEM slot, job
     static constexpr int SMEM = NB * MMA_STAGE + P * RAW_STAGE + BAR;
     static_assert(SMEM * CTAS + 1024 * CTAS <= 233472, "shared memory plan too large");
@@ -294,7 +300,8 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
     if (warp == 8) {
         // ---- MMA warp: one thread issues every stage's six MMAs once the stage is full
         if (lane == 0) {
-            const uint32_t idesc = instr_desc(2 * w, false);
+            const uint32_t idesc = instr_desc(PL::FUSED ? 2 * w : w, false), idneg = instr_desc(w, true);
+            const uint32_t t_re = tmem, t_im = tmem + 128;
             for (int s = 0; s < nst && ok; ++s) {
                 const int buf = s % NB;
                 if (!mbar_wait(mfull + 8 * buf, (s / NB) & 1)) {
@@ -305,14 +312,30 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
                 const uint32_t sa = sbase + buf * PL::MMA_STAGE, sb = sa + 4 * TC_PLANE_A;
                 const uint64_t a0 = smem_desc(sa), a1 = smem_desc(sa + TC_PLANE_A),
                                a2 = smem_desc(sa + 2 * TC_PLANE_A), a3 = smem_desc(sa + 3 * TC_PLANE_A);
-                const uint64_t b0 = smem_desc(sb), b1 = smem_desc(sb + PL::PLANE_B2),
-                               b2 = smem_desc(sb + 2 * PL::PLANE_B2), b3 = smem_desc(sb + 3 * PL::PLANE_B2);
-                mma_tf32(tmem, a0, b0, idesc, s > 0 ? 1u : 0u);    // Ar_hi [Br_hi | Bi_hi]
-                mma_tf32(tmem, a0, b1, idesc, 1u);                 // Ar_hi [Br_lo | Bi_lo]
-                mma_tf32(tmem, a1, b0, idesc, 1u);                 // Ar_lo [Br_hi | Bi_hi]
-                mma_tf32(tmem, a2, b2, idesc, 1u);                 // Ai_hi [-Bi_hi | Br_hi]
-                mma_tf32(tmem, a2, b3, idesc, 1u);                 // Ai_hi [-Bi_lo | Br_lo]
-                mma_tf32(tmem, a3, b2, idesc, 1u);                 // Ai_lo [-Bi_hi | Br_hi]
+                const uint64_t b0 = smem_desc(sb), b1 = smem_desc(sb + PL::PLANE_B),
+                               b2 = smem_desc(sb + 2 * PL::PLANE_B), b3 = smem_desc(sb + 3 * PL::PLANE_B);
+                const uint32_t first = s > 0 ? 1u : 0u;
+                if constexpr (PL::FUSED) {
+                    mma_tf32(tmem, a0, b0, idesc, first);          // Ar_hi [Br_hi | Bi_hi]
+                    mma_tf32(tmem, a0, b1, idesc, 1u);             // Ar_hi [Br_lo | Bi_lo]
+                    mma_tf32(tmem, a1, b0, idesc, 1u);             // Ar_lo [Br_hi | Bi_hi]
+                    mma_tf32(tmem, a2, b2, idesc, 1u);             // Ai_hi [-Bi_hi | Br_hi]
+                    mma_tf32(tmem, a2, b3, idesc, 1u);             // Ai_hi [-Bi_lo | Br_lo]
+                    mma_tf32(tmem, a3, b2, idesc, 1u);             // Ai_lo [-Bi_hi | Br_hi]
+                } else {                                           // b0..b3: Br_hi, Br_lo, Bi_hi, Bi_lo
+                    mma_tf32(t_re, a0, b0, idesc, first);          // Ar Br
+                    mma_tf32(t_re, a0, b1, idesc, 1u);
+                    mma_tf32(t_re, a1, b0, idesc, 1u);
+                    mma_tf32(t_re, a2, b2, idneg, 1u);             // - Ai Bi
+                    mma_tf32(t_re, a2, b3, idneg, 1u);
+                    mma_tf32(t_re, a3, b2, idneg, 1u);
+                    mma_tf32(t_im, a0, b2, idesc, first);          // Ar Bi
+                    mma_tf32(t_im, a0, b3, idesc, 1u);
+                    mma_tf32(t_im, a1, b2, idesc, 1u);
+                    mma_tf32(t_im, a2, b0, idesc, 1u);             // Ai Br
+                    mma_tf32(t_im, a2, b1, idesc, 1u);
+                    mma_tf32(t_im, a3, b0, idesc, 1u);
+                }
                 mma_commit(mempty + 8 * buf);
             }
         }
@@ -371,7 +394,10 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
                 if (conjB)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) v[e].im = -v[e].im;
-                put4_b(pa + 4 * TC_PLANE_A, PL::PLANE_B2, uoff, boff_bot, v);
+                if constexpr (PL::FUSED)
+                    put4_b(pa + 4 * TC_PLANE_A, PL::PLANE_B, uoff, boff_bot, v);
+                else
+                    put4(pa + 4 * TC_PLANE_A, PL::PLANE_B, uoff, v);
             }
         };
         for (int p = 0; p < P - 1; ++p) {           // prologue: P - 1 raw stages in flight
@@ -398,7 +424,8 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
 
     if (ok && warp < 8) {
         // epilogue: warp v reads TMEM lanes 32 (v % 4) .. + 31 (C rows); column chunks of 16
-        // alternate between warps v and v + 4; Cr sits in columns [0, w), Ci in [w, 2w)
+        // alternate between warps v and v + 4; Cr sits in columns [0, w), Ci in [w, 2w) (FUSED) or
+        // [128, 128 + w)
         const int qd = warp & 3, hf = warp >> 2;
         const int i = i0 + 32 * qd + lane;
         const int nch = w / 16;
@@ -406,7 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
             float re[16], im[16];
             const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(16 * c);
             tmem_ld16(ta, re);
-            tmem_ld16(ta + (uint32_t)w, im);
+            tmem_ld16(ta + (uint32_t)(PL::FUSED ? w : 128), im);
             if (i < J.m) {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {

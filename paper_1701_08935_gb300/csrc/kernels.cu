@@ -56,6 +56,15 @@ double prof_collect_ms() {
 }
 
 // ============================================================== batched GEMM
+// 8-byte asynchronous global -> shared copy; src_size 0 fills zeros (no global read)
+__device__ __forceinline__ void cp_async_8(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Job of a tile: the launch's tile map when it has one, else a binary search of tile0.
 __device__ __forceinline__ int find_job(const int32_t *tmap, const GJob *jobs, int njobs, int tile) {
     if (tmap) return tmap[tile];
@@ -82,8 +91,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
     if (tile >= g.ntiles[z]) return;
     const GJob *jobs = g.jobs[z];
     __shared__ int s_job;
-    __shared__ cx<T> As[BK][BM];
-    __shared__ cx<T> Bs[BK][BN];
+    // complex64: two buffers filled by cp.async; complex128: one buffer filled from registers
+    constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
+    __shared__ __align__(16) cx<T> As2[NBUF][BK][BM];
+    __shared__ __align__(16) cx<T> Bs2[NBUF][BK][BN];
+    auto &As = As2[0];
+    auto &Bs = Bs2[0];
     const int tid = threadIdx.x;
     if (tid == 0) s_job = find_job(g.tmap[z], jobs, g.njobs[z], tile);
     __syncthreads();
@@ -108,6 +121,59 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = mk<T>(0, 0);
 
+    if constexpr (sizeof(T) == 4) {
+        // complex64: double-buffered cp.async staging (zero fill at the edges), so the loads of
+        // k-tile s + 1 are in flight while tile s is consumed; conjugation is applied on read
+        const int nst = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+        auto issue = [&](int l0, int buf) {
+#pragma unroll
+            for (int q = 0; q < (BM * BK) / 256; ++q) {
+                const int e = tid + 256 * q;
+                int i, l;
+                if (J.ars == 1) { i = e % BM; l = e / BM; } else { l = e % BK; i = e / BK; }
+                const bool v = (i0 + i < J.m) && (l0 + l < kend);
+                const cx<T> *src = v ? A + (int64_t)(i0 + i) * J.ars + (int64_t)(l0 + l) * J.acs : A;
+                cp_async_8((uint32_t)__cvta_generic_to_shared(&As2[buf][l][i]), src, v);
+            }
+#pragma unroll
+            for (int q = 0; q < (BN * BK) / 256; ++q) {
+                const int e = tid + 256 * q;
+                int j, l;
+                if (J.brs == 1) { l = e % BK; j = e / BK; } else { j = e % BN; l = e / BN; }
+                const bool v = (j0 + j < J.n) && (l0 + l < kend);
+                const cx<T> *src = v ? B + (int64_t)(l0 + l) * J.brs + (int64_t)(j0 + j) * J.bcs : B;
+                cp_async_8((uint32_t)__cvta_generic_to_shared(&Bs2[buf][l][j]), src, v);
+            }
+        };
+        if (nst > 0) issue(kbeg, 0);
+        cp_async_commit_group();
+        for (int s = 0; s < nst; ++s) {
+            if (s + 1 < nst) issue(kbeg + (s + 1) * BK, (s + 1) & 1);
+            cp_async_commit_group();
+            cp_async_wait_group<1>();
+            __syncthreads();
+            const int b = s & 1;
+#pragma unroll 4
+            for (int l = 0; l < BK; ++l) {
+                cx<T> a[4], bv[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    a[r] = As2[b][l][ty + TY * r];
+                    if (conjA) a[r].im = -a[r].im;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    bv[c] = Bs2[b][l][tx + TX * c];
+                    if (conjB) bv[c].im = -bv[c].im;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) fma_acc(acc[r][c], a[r], bv[c]);
+            }
+            __syncthreads();
+        }
+    } else
     for (int l0 = kbeg; l0 < kend; l0 += BK) {
         // ---- stage A tile (BM x BK) and B tile (BK x BN)
 #pragma unroll
@@ -512,12 +578,12 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> g) {
     }
     __syncthreads();
     const RJob J = g.jobs[s_job];
-    const int r0 = (tile - J.tile0) * ROWS_PER_TILE;
+    const int r0 = (tile - J.tile0) * g.rpt;
     const int32_t *map = g.map + J.map;
     const int k = g.k;
     cx<T> *W = g.W[z];
     c128 *X = g.X[z];
-    for (int e = threadIdx.x; e < ROWS_PER_TILE * k; e += 256) {
+    for (int e = threadIdx.x; e < g.rpt * k; e += 256) {
         const int rr = e / k, c = e - rr * k;
         const int r = r0 + rr;
         if (r >= J.rows) break;
@@ -873,6 +939,56 @@ void launch_colnorm2(int64_t n, int64_t k, const c128 *X, int64_t ldx, double *o
     g_counters.launches += 2;
 }
 
+// ============================================================== square transposes
+template <class T>
+__global__ void __launch_bounds__(256) k_transpose_sq(EyeArgs<T> g) {
+    const int z = blockIdx.z;
+    const int tile = blockIdx.x;
+    if (tile >= g.ntiles) return;
+    __shared__ int s_job;
+    __shared__ cx<T> ta[32][33], tb[32][33];
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = g.njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const RJob J = g.jobs[s_job];
+    int loc = tile - J.tile0, bi = 0;
+    while (loc >= J.tr - bi) {            // row bi of the upper triangle holds tr - bi tile pairs
+        loc -= J.tr - bi;
+        ++bi;
+    }
+    const int bj = bi + loc;
+    const int64_t n = J.rows;
+    cx<T> *M = g.P[z] + J.dst;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i1 = 32 * bi + r, j1 = 32 * bj + tx;      // (bi, bj) tile
+        const int64_t i2 = 32 * bj + r, j2 = 32 * bi + tx;      // (bj, bi) tile
+        if (i1 < n && j1 < n) ta[r][tx] = M[i1 + j1 * n];
+        if (i2 < n && j2 < n) tb[r][tx] = M[i2 + j2 * n];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i1 = 32 * bi + r, j1 = 32 * bj + tx;
+        const int64_t i2 = 32 * bj + r, j2 = 32 * bi + tx;
+        if (i1 < n && j1 < n) M[i1 + j1 * n] = tb[tx][r];        // M(i1, j1) <- old M(j1, i1)
+        if (i2 < n && j2 < n) M[i2 + j2 * n] = ta[tx][r];
+    }
+}
+
+template <class T>
+void launch_transpose_sq(const EyeArgs<T> &g, int ninst, cudaStream_t st) {
+    if (g.ntiles == 0) return;
+    dim3 grid(g.ntiles, 1, ninst);
+    k_transpose_sq<T><<<grid, 256, 0, st>>>(g);
+    g_counters.launches++;
+}
+
 // explicit instantiations
 template void launch_gemm<double>(const GemmArgs<double> &, int, cudaStream_t, double);
 template void launch_gemm<float>(const GemmArgs<float> &, int, cudaStream_t, double);
@@ -885,6 +1001,8 @@ template void launch_extend_add<float>(const EaddArgs<float> &, int, cudaStream_
 template void launch_rows<double>(const RowArgs<double> &, int, cudaStream_t);
 template void launch_eye<double>(const EyeArgs<double> &, int, cudaStream_t);
 template void launch_eye<float>(const EyeArgs<float> &, int, cudaStream_t);
+template void launch_transpose_sq<double>(const EyeArgs<double> &, int, cudaStream_t);
+template void launch_transpose_sq<float>(const EyeArgs<float> &, int, cudaStream_t);
 template void launch_rows<float>(const RowArgs<float> &, int, cudaStream_t);
 
 }  // namespace zolo

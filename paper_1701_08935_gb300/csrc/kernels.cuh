@@ -1,5 +1,6 @@
 // Launch arguments and launchers of the device kernels.  Internal to the library.
 #pragma once
+#include <algorithm>
 #include "device.cuh"
 
 namespace zolo {
@@ -44,13 +45,15 @@ template <class T> struct EaddArgs {
 };
 
 enum { ROW_GATHER = 0, ROW_SCATTER = 1, ROW_EADD = 2, ROW_ZERO = 3 };
-constexpr int ROWS_PER_TILE = 8;
+// rows per CTA of the row kernels: about 2048 elements (8 per thread) for a block width k
+inline int rows_per_tile(int64_t k) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, 2048 / std::max<int64_t>(1, k))); }
 
 template <class T> struct RowArgs {
     const RJob *jobs;
     int njobs, ntiles;
     const int32_t *map;
     int mode, k;
+    int rpt;                             // rows per CTA tile (the schedule's rows_per_tile(k))
     int64_t ldw, ldx;
     cx<T> *W[MAX_INST];
     c128 *X[MAX_INST];
@@ -139,6 +142,10 @@ template <class T> struct EyeArgs {
     cx<T> *P[MAX_INST];
 };
 template <class T> void launch_eye(const EyeArgs<T> &g, int ninst, cudaStream_t st);
+// in-place transposes of square blocks: for each job, the rows x rows block at P[dst] (ld = rows);
+// the job's CTAs (tr = tiles per side, tile0 its first CTA) take the 32 x 32 tile pairs
+// (bi, bj), bi <= bj, in row order
+template <class T> void launch_transpose_sq(const EyeArgs<T> &g, int ninst, cudaStream_t st);
 void launch_spmm(const DevCSR &M, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, c128 s, bool acc,
                  cudaStream_t st);
 void launch_lincomb(const LinArgs &a, cudaStream_t st);

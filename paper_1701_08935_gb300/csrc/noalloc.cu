@@ -113,6 +113,7 @@ extern "C" int zolo_solve_noalloc(zolo_factor_h h, int32_t pole, int32_t herm, i
                 r.ntiles = o.L.ntiles;
                 r.map = (o.kind == SOP_EADD) ? h->d_rel : h->d_rows;
                 r.k = (int)k;
+                r.rpt = rows_per_tile(k);
                 r.ldw = k;
                 r.mode = (o.kind == SOP_EADD) ? ROW_EADD
                          : (o.kind == SOP_SCATTER_OUT ? ROW_SCATTER : (o.kind == SOP_ZERO ? ROW_ZERO : ROW_GATHER));
