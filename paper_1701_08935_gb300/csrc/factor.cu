@@ -158,6 +158,12 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
     } else if (allow_split && base > 0 && base * g_plan_ninst < 4 * 152) {
         factor = (4 * 152 + base * g_plan_ninst - 1) / (base * g_plan_ninst);
     }
+    // FMA tiles of skinny accumulating products (inner extent kk well above the row count,
+    // e.g. U_pu x_u of the backward solve at deep levels) run long, latency-bound k-loops:
+    // split kk into pieces of about twice the tile height however many tiles there are
+    auto skinny = [&](const GJob &j) {
+        return allow_split && !L.tc && (j.flags & (GJ_SUB | GJ_ACC)) && j.k >= 4 * std::max(j.m, L.bm) && j.k >= 128;
+    };
     int tiles = 0;
     if (L.tc) {                            // the tile width the tensor-core kernel derives per job
         L.wmax = 16;
@@ -171,6 +177,7 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
         if (j.m <= 0 || j.n <= 0 || j.k <= 0) continue;
         j.tm = (j.m + L.bm - 1) / L.bm;
         j.ks = factor > 1 ? split_of(j, factor) : 1;
+        if (skinny(j)) j.ks = std::max(j.ks, std::min(16, j.k / (2 * std::max(j.m, L.bm))));
         j.tile0 = tiles;
         const int nt = j.tm * ((j.n + L.bn - 1) / L.bn) * j.ks;
         tiles += nt;

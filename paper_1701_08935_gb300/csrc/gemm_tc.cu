@@ -30,7 +30,7 @@
 // that stage's "full" mbarrier.  A ninth warp issues each stage's six MMAs once it is full and
 // commits them to the stage's "empty" mbarrier, which the converters wait on before they
 // overwrite it, so the MMA issue never holds up the conversion.  The plan depends on the
-// widest tile of the launch (WMAX = 32, 64, 128: NB = 3, 2, 2 and P = 4, 4, 3), two CTAs per
+// widest tile of the launch (WMAX = 32, 64, 128: NB = 2 and P = 6, 4, 3), two CTAs per
 // SM; 128-wide tiles keep Cr and Ci in separate accumulators (twelve MMAs of N = w per
 // k-step) to fit.  Every wait on an mbarrier is bounded in time (2 s): on expiry the thread skips
 // its remaining waits, the CTA skips its epilogue, records ZOLO_ETIMEOUT in a device status
@@ -63,8 +63,8 @@ template <int WMAX> struct TcPlan {
     static constexpr int RAW_A = TC_BM * TC_BK * 8;                   // raw complex64 A stage (8 KB)
     static constexpr int RAW_STAGE = RAW_A + WMAX * TC_BK * 8;
     static constexpr int CTAS = 2;                                    // CTAs per SM
-    static constexpr int NB = WMAX <= 32 ? 3 : 2;                     // MMA stages
-    static constexpr int P = WMAX <= 64 ? 4 : 3;                      // raw stages in the ring
+    static constexpr int NB = 2;                                      // MMA stages
+    static constexpr int P = WMAX <= 32 ? 6 : (WMAX <= 64 ? 4 : 3);   // raw stages in the ring
     static constexpr int BAR = 128;                                   // mbarriers, TMEM slot, job
     static constexpr int SMEM = NB * MMA_STAGE + P * RAW_STAGE + BAR;
     static_assert(SMEM * CTAS + 1024 * CTAS <= 233472, "shared memory plan too large");
