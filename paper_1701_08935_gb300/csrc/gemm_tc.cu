@@ -435,19 +435,29 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
             tmem_ld16(ta, re);
             tmem_ld16(ta + (uint32_t)(PL::FUSED ? w : 128), im);
             if (i < J.m) {
+                // accumulating products: all 16 loads first, then the stores (an interleaved
+                // read-modify-write would wait one global round trip per element)
+                if ((sub || add) && !atom) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int j = j0 + 16 * c + jj;
+                        if (j < J.n) {
+                            const c64 o = C[(int64_t)i * J.crs + (int64_t)j * J.ccs];
+                            re[jj] = sub ? o.re - re[jj] : o.re + re[jj];
+                            im[jj] = sub ? o.im - im[jj] : o.im + im[jj];
+                        }
+                    }
+                }
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
                     const int j = j0 + 16 * c + jj;
                     if (j >= J.n) continue;
                     c64 *q = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
-                    const float vr = sub ? -re[jj] : re[jj], vi = sub ? -im[jj] : im[jj];
                     if (atom) {
+                        const float vr = sub ? -re[jj] : re[jj], vi = sub ? -im[jj] : im[jj];
                         atomicAdd(reinterpret_cast<float2 *>(q), make_float2(vr, vi));
-                    } else if (sub || add) {
-                        const c64 o = *q;
-                        *q = mk<float>(o.re + vr, o.im + vi);
                     } else {
-                        *q = mk<float>(vr, vi);
+                        *q = mk<float>(re[jj], im[jj]);
                     }
                 }
             }

@@ -216,6 +216,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
     }
     cx<T> *__restrict__ C = g.C[z] + J.c;
     const bool sub = J.flags & GJ_SUB, add = J.flags & GJ_ACC, atom = J.ks > 1;
+    // Accumulating products read every C element of the thread first (16 independent loads in
+    // flight) and only then write: interleaved read-modify-writes would make each load wait for
+    // the previous store, one global round trip per element.
+    if ((sub || add) && !atom) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = i0 + ty + TY * r;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + tx + TX * c;
+                if (i < J.m && j < J.n) {
+                    const cx<T> o = C[(int64_t)i * J.crs + (int64_t)j * J.ccs];
+                    acc[r][c] = sub ? o - acc[r][c] : o + acc[r][c];
+                }
+            }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int i = i0 + ty + TY * r;
@@ -225,12 +242,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
             const int j = j0 + tx + TX * c;
             if (j >= J.n) continue;
             cx<T> *p = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
-            const cx<T> v = sub ? mk<T>(-acc[r][c].re, -acc[r][c].im) : acc[r][c];
             if (atom) {
+                const cx<T> v = sub ? mk<T>(-acc[r][c].re, -acc[r][c].im) : acc[r][c];
                 atomicAdd(&p->re, v.re);
                 atomicAdd(&p->im, v.im);
             } else {
-                *p = (sub || add) ? (*p + v) : v;
+                *p = acc[r][c];
             }
         }
     }
@@ -340,6 +357,22 @@ __global__ void __launch_bounds__(256) k_gemm_c64(GemmArgs<float> g) {
     }
     c64 *__restrict__ C = g.C[z] + J.c;
     const bool sub = J.flags & GJ_SUB, add = J.flags & GJ_ACC, atom = J.ks > 1;
+    // read all C elements of the thread before any write (see k_gemm)
+    if ((sub || add) && !atom) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + (c < 2 ? tx * 2 + c : 32 + tx * 2 + (c - 2));
+                if (i < J.m && j < J.n) {
+                    const c64 o = C[(int64_t)i * J.crs + (int64_t)j * J.ccs];
+                    acc[r][c][0] = sub ? o.re - acc[r][c][0] : o.re + acc[r][c][0];
+                    acc[r][c][1] = sub ? o.im - acc[r][c][1] : o.im + acc[r][c][1];
+                }
+            }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
@@ -349,11 +382,11 @@ __global__ void __launch_bounds__(256) k_gemm_c64(GemmArgs<float> g) {
             const int j = j0 + (c < 2 ? tx * 2 + c : 32 + tx * 2 + (c - 2));
             if (j >= J.n) continue;
             c64 *p = C + (int64_t)i * J.crs + (int64_t)j * J.ccs;
-            const c64 v = sub ? mk<float>(-acc[r][c][0], -acc[r][c][1]) : mk<float>(acc[r][c][0], acc[r][c][1]);
             if (atom) {
-                atomicAdd(reinterpret_cast<float2 *>(p), make_float2(v.re, v.im));
+                const float vr = sub ? -acc[r][c][0] : acc[r][c][0], vi = sub ? -acc[r][c][1] : acc[r][c][1];
+                atomicAdd(reinterpret_cast<float2 *>(p), make_float2(vr, vi));
             } else {
-                *p = (sub || add) ? (*p + v) : v;
+                *p = mk<float>(acc[r][c][0], acc[r][c][1]);
             }
         }
     }
@@ -542,12 +575,20 @@ __global__ void __launch_bounds__(256) k_extend_add(EaddArgs<T> g) {
     const int i = bi + (threadIdx.x & 31);
     if (i >= J.rows) return;
     const int ri = rel[i];
-    for (int jj = threadIdx.x >> 5; jj < 32; jj += 8) {
-        const int j = bj + jj;
-        if (j >= J.rows) break;
-        cx<T> *p = P + ri + (int64_t)rel[j] * J.ld_dst;
-        *p = *p + S[i + (int64_t)j * J.ld_src];
+    cx<T> v[4];
+    cx<T> *p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {                    // loads first, then the stores
+        const int j = bj + (threadIdx.x >> 5) + 8 * q;
+        p[q] = nullptr;
+        if (j < J.rows) {
+            p[q] = P + ri + (int64_t)rel[j] * J.ld_dst;
+            v[q] = *p[q] + S[i + (int64_t)j * J.ld_src];
+        }
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (p[q]) *p[q] = v[q];
 }
 
 template <class T>
@@ -583,6 +624,28 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> g) {
     const int k = g.k;
     cx<T> *W = g.W[z];
     c128 *X = g.X[z];
+    if (g.mode == ROW_EADD) {
+        // batches of 8 elements per thread: all loads, then the stores (an interleaved
+        // read-modify-write would wait one global round trip per element)
+        for (int e0 = 0; e0 < g.rpt * k; e0 += 8 * 256) {
+            cx<T> v[8];
+            cx<T> *p[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = e0 + threadIdx.x + 256 * q;
+                const int rr = e / k, c = e - rr * k, r = r0 + rr;
+                p[q] = nullptr;
+                if (e < g.rpt * k && r < J.rows) {
+                    p[q] = W + J.dst + (int64_t)map[r] * g.ldw + c;
+                    v[q] = *p[q] + W[J.src + (int64_t)r * g.ldw + c];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (p[q]) *p[q] = v[q];
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < g.rpt * k; e += 256) {
         const int rr = e / k, c = e - rr * k;
         const int r = r0 + rr;
@@ -591,11 +654,8 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> g) {
             W[J.dst + (int64_t)r * g.ldw + c] = cvt<T>(X[(int64_t)map[r] * g.ldx + c]);
         } else if (g.mode == ROW_SCATTER) {
             X[(int64_t)map[r] * g.ldx + c] = cvt<double>(W[J.src + (int64_t)r * g.ldw + c]);
-        } else if (g.mode == ROW_ZERO) {
-            W[J.dst + (int64_t)r * g.ldw + c] = mk<T>(0, 0);
         } else {
-            cx<T> *p = W + J.dst + (int64_t)map[r] * g.ldw + c;
-            *p = *p + W[J.src + (int64_t)r * g.ldw + c];
+            W[J.dst + (int64_t)r * g.ldw + c] = mk<T>(0, 0);
         }
     }
 }
