@@ -203,7 +203,12 @@ Launch add_rows(std::vector<RJob> &all, const std::vector<RJob> &jobs, int tile_
         if (j.rows <= 0) continue;
         j.tile0 = tiles;
         j.tr = (j.rows + tile_rows - 1) / tile_rows;
-        tiles += square ? j.tr * j.tr : j.tr;
+        const int nt = square ? j.tr * j.tr : j.tr;
+        tiles += nt;
+        if (g_plan_tmap) {                 // tile -> job map (saves each CTA a binary search)
+            if (L.tmoff < 0) L.tmoff = (int64_t)g_plan_tmap->size();
+            g_plan_tmap->insert(g_plan_tmap->end(), nt, (int32_t)L.cnt);
+        }
         all.push_back(j);
         L.cnt++;
     }
@@ -481,7 +486,10 @@ int build_factor_plan(zolo_factor_s *h, const zolo_csr *A, const zolo_csr *B) {
                     RJob j = rjob(0, h->f_finv[sn] + (int64_t)half * np * np, 0, np);
                     j.tr = (np + 31) / 32;
                     j.tile0 = tiles;
-                    tiles += j.tr * (j.tr + 1) / 2;
+                    const int nt = j.tr * (j.tr + 1) / 2;
+                    tiles += nt;
+                    if (tp.tmoff < 0) tp.tmoff = (int64_t)ftm.size();
+                    ftm.insert(ftm.end(), nt, (int32_t)tp.cnt);
                     ej.push_back(j);
                     tp.cnt++;
                 }
@@ -577,6 +585,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                 EaddArgs<T> ea;
                 std::memset(&ea, 0, sizeof(ea));
                 ea.jobs = h->d_ejobs + E.off;
+                ea.tmap = E.tmoff >= 0 ? h->d_ftmap + E.tmoff : nullptr;
                 ea.njobs = E.cnt;
                 ea.ntiles = E.ntiles;
                 ea.rel = h->d_rel;
@@ -629,6 +638,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
             EyeArgs<T> ey;
             std::memset(&ey, 0, sizeof(ey));
             ey.jobs = h->d_ejobs + F.eye.off;
+            ey.tmap = F.eye.tmoff >= 0 ? h->d_ftmap + F.eye.tmoff : nullptr;
             ey.njobs = F.eye.cnt;
             ey.ntiles = F.eye.ntiles;
             for (int z = 0; z < ni; ++z) ey.P[z] = finv[z];
@@ -662,6 +672,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
             EyeArgs<T> tp;                                  // row-major -> column-major
             std::memset(&tp, 0, sizeof(tp));
             tp.jobs = h->d_ejobs + F.tpose.off;
+            tp.tmap = F.tpose.tmoff >= 0 ? h->d_ftmap + F.tpose.tmoff : nullptr;
             tp.njobs = F.tpose.cnt;
             tp.ntiles = F.tpose.ntiles;
             for (int z = 0; z < ni; ++z) tp.P[z] = finv[z];
@@ -900,6 +911,7 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                 RowArgs<T> r;
                 std::memset(&r, 0, sizeof(r));
                 r.jobs = h->d_rjobs + o.L.off;
+                r.tmap = o.L.tmoff >= 0 ? h->d_stmap + o.L.tmoff : nullptr;
                 r.njobs = o.L.cnt;
                 r.ntiles = o.L.ntiles;
                 r.map = (o.kind == SOP_EADD) ? h->d_rel : h->d_rows;

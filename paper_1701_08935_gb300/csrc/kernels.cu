@@ -65,6 +65,18 @@ template <int N> __device__ __forceinline__ void cp_async_wait_group() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Job of a row / extend-add / identity / transpose tile: the launch's tile map when it has
+// one, else a binary search of tile0.
+__device__ __forceinline__ int find_rjob(const int32_t *tmap, const RJob *jobs, int njobs, int tile) {
+    if (tmap) return tmap[tile];
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Job of a tile: the launch's tile map when it has one, else a binary search of tile0.
 __device__ __forceinline__ int find_job(const int32_t *tmap, const GJob *jobs, int njobs, int tile) {
     if (tmap) return tmap[tile];
@@ -557,14 +569,7 @@ __global__ void __launch_bounds__(256) k_extend_add(EaddArgs<T> g) {
     const int tile = blockIdx.x;
     if (tile >= g.ntiles) return;
     __shared__ int s_job;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = g.njobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (g.jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-        }
-        s_job = lo;
-    }
+    if (threadIdx.x == 0) s_job = find_rjob(g.tmap, g.jobs, g.njobs, tile);
     __syncthreads();
     const RJob J = g.jobs[s_job];
     const int t = tile - J.tile0;
@@ -609,14 +614,7 @@ __global__ void __launch_bounds__(256) k_rows(RowArgs<T> g) {
     const int tile = blockIdx.x;
     if (tile >= g.ntiles) return;
     __shared__ int s_job;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = g.njobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (g.jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-        }
-        s_job = lo;
-    }
+    if (threadIdx.x == 0) s_job = find_rjob(g.tmap, g.jobs, g.njobs, tile);
     __syncthreads();
     const RJob J = g.jobs[s_job];
     const int r0 = (tile - J.tile0) * g.rpt;
@@ -675,14 +673,7 @@ __global__ void __launch_bounds__(256) k_eye_blocks(EyeArgs<T> g) {
     const int tile = blockIdx.x;
     if (tile >= g.ntiles) return;
     __shared__ int s_job;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = g.njobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (g.jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-        }
-        s_job = lo;
-    }
+    if (threadIdx.x == 0) s_job = find_rjob(g.tmap, g.jobs, g.njobs, tile);
     __syncthreads();
     const RJob J = g.jobs[s_job];
     const int i = (tile - J.tile0) * 256 + threadIdx.x;
@@ -1007,14 +998,7 @@ __global__ void __launch_bounds__(256) k_transpose_sq(EyeArgs<T> g) {
     if (tile >= g.ntiles) return;
     __shared__ int s_job;
     __shared__ cx<T> ta[32][33], tb[32][33];
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = g.njobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (g.jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-        }
-        s_job = lo;
-    }
+    if (threadIdx.x == 0) s_job = find_rjob(g.tmap, g.jobs, g.njobs, tile);
     __syncthreads();
     const RJob J = g.jobs[s_job];
     int loc = tile - J.tile0, bi = 0;

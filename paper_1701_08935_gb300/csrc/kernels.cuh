@@ -39,6 +39,7 @@ template <class T> struct AsmArgs {
 
 template <class T> struct EaddArgs {
     const RJob *jobs;
+    const int32_t *tmap;                 // job of every tile, or null (binary search)
     int njobs, ntiles;
     const int32_t *rel;
     cx<T> *pool[MAX_INST];
@@ -50,6 +51,7 @@ inline int rows_per_tile(int64_t k) { return (int)std::max<int64_t>(1, std::min<
 
 template <class T> struct RowArgs {
     const RJob *jobs;
+    const int32_t *tmap;                 // job of every tile, or null (binary search)
     int njobs, ntiles;
     const int32_t *map;
     int mode, k;
@@ -138,6 +140,7 @@ template <class T> void launch_rows(const RowArgs<T> &g, int ninst, cudaStream_t
 // unit diagonals: for each job, P[dst + i (rows + 1)] = 1 and P[dst + rows^2 + i (rows + 1)] = 1
 template <class T> struct EyeArgs {
     const RJob *jobs;
+    const int32_t *tmap;                 // job of every tile, or null (binary search)
     int njobs, ntiles;
     cx<T> *P[MAX_INST];
 };

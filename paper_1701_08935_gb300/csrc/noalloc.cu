@@ -109,6 +109,7 @@ extern "C" int zolo_solve_noalloc(zolo_factor_h h, int32_t pole, int32_t herm, i
                 RowArgs<double> r;
                 std::memset(&r, 0, sizeof(r));
                 r.jobs = h->d_rjobs + o.L.off;
+                r.tmap = o.L.tmoff >= 0 ? h->d_stmap + o.L.tmoff : nullptr;
                 r.njobs = o.L.cnt;
                 r.ntiles = o.L.ntiles;
                 r.map = (o.kind == SOP_EADD) ? h->d_rel : h->d_rows;
