@@ -99,8 +99,9 @@ constexpr double TC_MIN_ROWS = 128.0;
 // Append a launch of GEMM jobs (empty products dropped) and return its descriptor.
 // Tiles of a complex64 launch: the tensor-core kernel (128 x <= 128) when its jobs average
 // >= TC_MIN_ROWS rows (every launch with ZOLO_TC_ALWAYS, none with ZOLO_TC_OFF); otherwise
-// FP32-FMA tiles of 128 x 64 when they average >= 256 rows, 32 x 128 when <= 40, else
-// 64 x 64.  Complex128 launches take 64 x 64.  With allow_split, a launch with fewer than ~4 waves
+// FP32-FMA tiles: 32 wide when no job has more than 32 columns (32, 64 or 128 rows by the
+// average row count), else 128 x 64 when they average >= 256 rows, 32 x 128 when <= 40,
+// else 64 x 64.  Complex128 launches take 64 x 64.  With allow_split, a launch with fewer than ~4 waves
 // of tiles splits the kk extent of its accumulating jobs (GJ_SUB / GJ_ACC, kk >= g_plan_split_min) over
 // several CTAs (atomic adds).
 Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool allow_split = false) {
@@ -119,6 +120,13 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
     if (g_plan_c64 && cnt && msum / cnt <= 40.0) {       // few pivot rows: 32 x 128 FMA tiles
         L.bm = 32;
         L.bn = 128;
+    }
+    int nmax = 0;
+    for (const GJob &j : jobs_in)
+        if (j.m > 0 && j.n > 0 && j.k > 0) nmax = std::max(nmax, j.n);
+    if (g_plan_c64 && cnt && nmax <= 32) {                // narrow blocks: 32-wide FMA tiles
+        L.bn = 32;
+        L.bm = msum / cnt <= 40.0 ? 32 : (msum / cnt <= 96.0 ? 64 : 128);
     }
     if (g_plan_c64 && cnt &&
         (g_plan_tc == ZOLO_TC_ALWAYS || (g_plan_tc == ZOLO_TC_AUTO && msum / cnt >= TC_MIN_ROWS))) {

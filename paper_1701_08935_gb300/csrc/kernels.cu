@@ -97,7 +97,7 @@ __device__ __forceinline__ int find_job(const int32_t *tmap, const GJob *jobs, i
 // RE: the operands hold real values (zero imaginary parts) -- one real FMA per product
 // instead of four; the imaginary parts of C are left as they are.
 template <class T, int BM, int BN, int BK, bool RE = false>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T> g) {
+__global__ void __launch_bounds__(BM * BN / 16, sizeof(T) == 4 ? 3 * 4096 / (BM * BN) : 1) k_gemm(GemmArgs<T> g) {
     const int z = blockIdx.z;
     const int tile = blockIdx.x;
     if (tile >= g.ntiles[z]) return;
@@ -124,8 +124,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
     const cx<T> *__restrict__ A = g.A[z] + J.a;
     const cx<T> *__restrict__ B = g.B[z] + J.b;
     const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
-    constexpr int TX = BN / 4, TY = BM / 4;             // 256 threads, 4 x 4 outputs each
-    static_assert(TX * TY == 256, "tile must give 256 threads");
+    constexpr int TX = BN / 4, TY = BM / 4;             // TX * TY threads, 4 x 4 outputs each
+    constexpr int NT = TX * TY;
+    static_assert((BM * BK) % NT == 0 && (BN * BK) % NT == 0, "tile must split evenly over the threads");
     const int tx = tid % TX, ty = tid / TX;
     cx<T> acc[4][4];
 #pragma unroll
@@ -139,8 +140,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
         const int nst = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
         auto issue = [&](int l0, int buf) {
 #pragma unroll
-            for (int q = 0; q < (BM * BK) / 256; ++q) {
-                const int e = tid + 256 * q;
+            for (int q = 0; q < (BM * BK) / NT; ++q) {
+                const int e = tid + NT * q;
                 int i, l;
                 if (J.ars == 1) { i = e % BM; l = e / BM; } else { l = e % BK; i = e / BK; }
                 const bool v = (i0 + i < J.m) && (l0 + l < kend);
@@ -148,8 +149,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
                 cp_async_8((uint32_t)__cvta_generic_to_shared(&As2[buf][l][i]), src, v);
             }
 #pragma unroll
-            for (int q = 0; q < (BN * BK) / 256; ++q) {
-                const int e = tid + 256 * q;
+            for (int q = 0; q < (BN * BK) / NT; ++q) {
+                const int e = tid + NT * q;
                 int j, l;
                 if (J.brs == 1) { l = e % BK; j = e / BK; } else { j = e % BN; l = e / BN; }
                 const bool v = (j0 + j < J.n) && (l0 + l < kend);
@@ -189,8 +190,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
     for (int l0 = kbeg; l0 < kend; l0 += BK) {
         // ---- stage A tile (BM x BK) and B tile (BK x BN)
 #pragma unroll
-        for (int q = 0; q < (BM * BK) / 256; ++q) {
-            const int e = tid + 256 * q;
+        for (int q = 0; q < (BM * BK) / NT; ++q) {
+            const int e = tid + NT * q;
             int i, l;
             if (J.ars == 1) { i = e % BM; l = e / BM; } else { l = e % BK; i = e / BK; }
             cx<T> v = mk<T>(0, 0);
@@ -198,8 +199,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_gemm(GemmArgs<T
             As[l][i] = conjA ? conj(v) : v;
         }
 #pragma unroll
-        for (int q = 0; q < (BN * BK) / 256; ++q) {
-            const int e = tid + 256 * q;
+        for (int q = 0; q < (BN * BK) / NT; ++q) {
+            const int e = tid + NT * q;
             int j, l;
             if (J.brs == 1) { l = e % BK; j = e / BK; } else { j = e % BN; l = e / BN; }
             cx<T> v = mk<T>(0, 0);
@@ -422,6 +423,12 @@ void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops)
         tc = (g.bm == 128 && g.bn == 128);
         if (tc)
             launch_gemm_tc(g, grid, st);
+        else if (g.bn == 32 && g.bm == 32)               // narrow blocks (n <= 32): no padded columns
+            k_gemm<T, 32, 32, 8><<<grid, 64, 0, st>>>(g);
+        else if (g.bn == 32 && g.bm == 64)
+            k_gemm<T, 64, 32, 8><<<grid, 128, 0, st>>>(g);
+        else if (g.bn == 32)
+            k_gemm<T, 128, 32, 16><<<grid, 256, 0, st>>>(g);
         else if (g.bm == G2_BM)
             k_gemm_c64<<<grid, 256, 0, st>>>(g);
         else if (g.bm == 32)
