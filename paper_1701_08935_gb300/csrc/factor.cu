@@ -128,8 +128,14 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
         L.bn = 32;
         L.bm = msum / cnt <= 40.0 ? 32 : (msum / cnt <= 96.0 ? 64 : 128);
     }
+    // narrow blocks: the tensor-core CTA's fixed cost (tensor-memory allocation, barrier set-up,
+    // pipeline fill) outweighs a short inner extent, so those launches need kk >= 256 on average
+    double ksum = 0.0;
+    for (const GJob &j : jobs_in)
+        if (j.m > 0 && j.n > 0 && j.k > 0) ksum += j.k;
+    const bool tc_k_ok = nmax > 32 || (cnt && ksum / cnt >= 256.0);
     if (g_plan_c64 && cnt &&
-        (g_plan_tc == ZOLO_TC_ALWAYS || (g_plan_tc == ZOLO_TC_AUTO && msum / cnt >= TC_MIN_ROWS))) {
+        (g_plan_tc == ZOLO_TC_ALWAYS || (g_plan_tc == ZOLO_TC_AUTO && msum / cnt >= TC_MIN_ROWS && tc_k_ok))) {
         L.bm = 128;
         L.bn = 128;
         L.tc = true;

@@ -108,11 +108,13 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
+// Non-blocking test of a phase (test_wait never suspends the thread, so a completed phase is
+// seen at the next poll).
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
         : "r"(mbar), "r"(parity)
@@ -126,9 +128,8 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for the given phase parity, for TC_WAIT_NS of wall time at most (try_wait may
-// suspend the thread for a system-dependent time per poll, so the bound is on time, not
-// on polls); false when the limit ran out.
+// Wait for the given phase parity, for TC_WAIT_NS of wall time at most (the bound is on
+// time, not on polls); false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     const uint64_t t0 = global_ns();
     while (!mbar_try(mbar, parity))
