@@ -16,7 +16,7 @@ from two FP64 inertia counts, FP64 residuals, B-orthonormality, distinct eigenva
 R(B^-1 A) x = R(lam) x on sampled pairs); value is 0 when a check fails.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                  [--workload lap96|peierls64|lap48] [--compare-fp64] [--locate]
+                  [--workload lap96|peierls64|lap48] [--no-fp64-compare] [--locate]
   python bench.py --impl reference      # the CPU oracle on a bounded sample
 """
 import argparse
@@ -290,6 +290,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     Z.profile_begin(0)
+    torch.cuda.profiler.start()            # a profiler attached with --profile-from-start off sees the timed steps only
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     conv, flops_alg, stats, last = 0, 0.0, None, None
@@ -301,6 +302,7 @@ def run_ours(args):
         flops_alg += st["flops_factor"] + st["flops_solve"] * st["solve_cols"]
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     prof = Z.profile_end()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -373,7 +375,7 @@ def run_ours(args):
         del Vd
 
     fp64_compare = None
-    if args.compare_fp64 and prec == Z.PREC_MIXED and rank == 0:
+    if not args.no_fp64_compare and prec == Z.PREC_MIXED and rank == 0:
         fp64_compare = compare_fp64(Z, pen, sym, W, am, ap, bm, bp, a, b, count_b - count_a, X0, ev)
 
     if rank != 0:
@@ -424,29 +426,46 @@ def roofline(Z, prec, gp, stp, flops_alg, t_step_ms):
     """The dominant kernel against its roofline, from the one step whose GEMM launches were
     bracketed by CUDA events on the launching stream.  Algorithmic flops (LU flops of the
     fronts + 16 nnz(L) per solve column, the per-unit counts of the scope table) are split
-    between the GEMM engines in proportion to their executed flops (8 m n k per job)."""
+    between the GEMM engines in proportion to their executed flops (8 m n k per job);
+    algorithmic bytes per job are A and B read once and C written (and read when the job
+    accumulates).  The bound is the larger of bytes / measured HBM bandwidth and algorithmic
+    flops / tensor peak over the kernel's launches (a lower bound on the sum of per-launch
+    maxima, so the fraction is conservative)."""
     gemm_s = gp["gemm_ms"] / 1e3
     tc_s = gp["tc_ms"] / 1e3
     fma_s = gemm_s - tc_s
     fma_flops = gp["gemm_flops"] - gp["tc_flops"]
     alg_over_exec = flops_alg / gp["gemm_flops"] if gp["gemm_flops"] > 0 else None
+    hbm = _measured("hbm_gbs", 6800.0)
     if prec == Z.PREC_MIXED and tc_s > 0:
         # tcgen05 kind::tf32 with a 3xTF32 split: 3 TF32 products per real product, so the
         # complex64 ceiling is the TF32 dense peak / 3; the TF32 peak is the measured bf16 peak
         # (sustained: the kernel runs inside a long step) x the nominal TF32/bf16 ratio 1.1/2.25
         tf32_peak = _measured("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
-        ach = gp["tc_flops"] * (alg_over_exec or 1.0) / tc_s / 1e12
-        roof = {"bound": "tensor", "kernel": "k_gemm_tc (tcgen05.mma kind::tf32, 3xTF32 complex64 front / solve products)",
-                "achieved": ach, "peak": tf32_peak / 3.0, "unit": "TFLOP/s", "traffic": None,
-                "achieved_def": "algorithmic flops of the tensor-core GEMM jobs (their executed 8 m n k scaled by the "
-                                "step's algorithmic / executed ratio) / their summed device time (CUDA events)",
-                "peak_def": "of measured: bf16_tflops_sustained x 1.1/2.25 (nominal TF32/bf16) / 3 (3xTF32)",
-                "executed_tflops": gp["tc_flops"] / tc_s / 1e12,
-                "ms_per_step": gp["tc_ms"], "launches_per_step": gp["tc_launches"]}
+        peak_t = tf32_peak / 3.0
+        flops_tc = gp["tc_flops"] * (alg_over_exec or 1.0)
+        t_flops = flops_tc / (peak_t * 1e12)
+        t_bytes = gp["tc_bytes"] / (hbm * 1e9)
+        if t_bytes >= t_flops:
+            roof = {"bound": "hbm", "achieved": gp["tc_bytes"] / tc_s / 1e9, "peak": hbm, "unit": "GB/s",
+                    "achieved_def": "algorithmic bytes of the tensor-core GEMM jobs (A, B once, C written / "
+                                    "read-modify-written) / their summed device time (CUDA events)",
+                    "peak_def": "of measured: hbm_gbs"}
+        else:
+            roof = {"bound": "tensor", "achieved": flops_tc / tc_s / 1e12, "peak": peak_t, "unit": "TFLOP/s",
+                    "achieved_def": "algorithmic flops of the tensor-core GEMM jobs / their summed device time",
+                    "peak_def": "of measured: bf16_tflops_sustained x 1.1/2.25 (nominal TF32/bf16) / 3 (3xTF32)"}
+        roof.update({"kernel": "k_gemm_tc (tcgen05.mma kind::tf32, 3xTF32 complex64 front / solve products)",
+                     "traffic": None, "t_roof_over_t": max(t_flops, t_bytes) / tc_s,
+                     "tensor_view": {"achieved_tflops": flops_tc / tc_s / 1e12, "peak_tflops": peak_t,
+                                     "frac": flops_tc / tc_s / 1e12 / peak_t},
+                     "hbm_view": {"achieved_gbs": gp["tc_bytes"] / tc_s / 1e9, "peak_gbs": hbm,
+                                  "frac": gp["tc_bytes"] / tc_s / 1e9 / hbm},
+                     "ms_per_step": gp["tc_ms"], "launches_per_step": gp["tc_launches"]})
     else:
         peak = FP32_PEAK_TFLOPS if prec == Z.PREC_MIXED else _measured("fp64_tflops", 1.10)
         ach = fma_flops * (alg_over_exec or 1.0) / fma_s / 1e12 if fma_s > 0 else None
-        roof = {"bound": "alu", "kernel": "k_gemm_c64 / k_gemm<float> (complex64 products, FP32 FFMA)"
+        roof = {"bound": "alu", "kernel": "k_gemm (complex64 products, FP32 FFMA)"
                 if prec == Z.PREC_MIXED else "k_gemm<double> (complex128 products, FP64 FMA)",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "traffic": None,
                 "achieved_def": "algorithmic flops of the GEMM jobs / their summed device time",
@@ -458,6 +477,7 @@ def roofline(Z, prec, gp, stp, flops_alg, t_step_ms):
                             "gemm_fma": fma_s * 1e3, "other": t_step_ms - gp["gemm_ms"],
                             "launches": gp["launches"], "gemm_launches": gp["gemm_launches"]}
     roof["fma_gemm"] = {"tflops_alg": fma_flops * (alg_over_exec or 1.0) / fma_s / 1e12 if fma_s > 0 else None,
+                        "gbs": (gp["gemm_bytes"] - gp["tc_bytes"]) / fma_s / 1e9 if fma_s > 0 else None,
                         "frac_of_fp32_alu": (fma_flops * (alg_over_exec or 1.0) / fma_s / 1e12 / FP32_PEAK_TFLOPS)
                         if fma_s > 0 and prec == Z.PREC_MIXED else None}
     roof["step_tflops_alg"] = flops_alg / (t_step_ms / 1e3) / 1e12 if t_step_ms > 0 else None
@@ -627,8 +647,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lap96", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--compare-fp64", action="store_true",
-                    help="after the mixed measurement, run one step of the same workload in complex128")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the one complex128 step of the same workload that follows the mixed measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--locate", action="store_true", help="locate the eigengaps by inertia counts and exit")
     args = ap.parse_args()

@@ -342,6 +342,10 @@ int  zolo_profile_end(void *stream, int64_t *launches, int64_t *gemm_launches, d
  * zolo_profile_begin and zolo_profile_end: launches, summed device time (ms), executed
  * flops (8 m n k per job).  Host values only; never fails.                         */
 int  zolo_profile_tc(int64_t *launches, double *ms, double *flops);
+/* Algorithmic bytes of the timed GEMM launches between the last zolo_profile_begin and
+ * zolo_profile_end (each job's A and B read once, C written, and read too when the job
+ * accumulates), all of them and the tensor-core subset.  Host values only.          */
+int  zolo_profile_bytes(double *gemm_bytes, double *tc_bytes);
 
 #ifdef __cplusplus
 }

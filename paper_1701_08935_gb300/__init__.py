@@ -110,6 +110,7 @@ _sig("zolo_inertia", C.c_int, [_P(Csr), _P(Csr), _vp, _P(Opts), _i32, _vp, _vp, 
 _sig("zolo_profile_begin", C.c_int, [_i32])
 _sig("zolo_profile_end", C.c_int, [_vp, _P(_i64), _P(_i64), _P(_dbl), _P(_dbl)])
 _sig("zolo_profile_tc", C.c_int, [_P(_i64), _P(_dbl), _P(_dbl)])
+_sig("zolo_profile_bytes", C.c_int, [_P(_dbl), _P(_dbl)])
 _sig("zolo_factor_destroy", None, [_vp])
 _sig("zolo_factor_get_stats", C.c_int, [_vp, _P(Stats)])
 _sig("zolo_solve", C.c_int, [_vp, _i32, _i32, _i64, _vp, _i64, _vp, _i64, _vp])
@@ -129,7 +130,7 @@ EXPORTED = ["zolo_opts_default", "zolo_strerror", "zolo_last_error", "zolo_versi
             "zolo_filter_get_info", "zolo_filter_eval", "zolo_filter_destroy", "zolo_analyze",
             "zolo_symbolic_get_info", "zolo_symbolic_export", "zolo_symbolic_destroy", "zolo_factor",
             "zolo_refactor", "zolo_inertia", "zolo_solve_noalloc", "zolo_profile_begin", "zolo_profile_end",
-            "zolo_profile_tc", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
+            "zolo_profile_tc", "zolo_profile_bytes", "zolo_factor_destroy", "zolo_factor_get_stats", "zolo_solve", "zolo_matmul",
             "zolo_apply_inner", "zolo_apply", "zolo_eigs_factored", "zolo_eigs", "zolo_eigs_slices"]
 
 
@@ -302,8 +303,11 @@ def profile_end(stream=None):
            "zolo_profile_end")
     tn, tms, tfl = _i64(0), _dbl(0), _dbl(0)
     _check(lib.zolo_profile_tc(C.byref(tn), C.byref(tms), C.byref(tfl)), "zolo_profile_tc")
+    gb, tb = _dbl(0), _dbl(0)
+    _check(lib.zolo_profile_bytes(C.byref(gb), C.byref(tb)), "zolo_profile_bytes")
     return {"launches": n.value, "gemm_launches": ng.value, "gemm_ms": ms.value, "gemm_flops": fl.value,
-            "tc_launches": tn.value, "tc_ms": tms.value, "tc_flops": tfl.value}
+            "tc_launches": tn.value, "tc_ms": tms.value, "tc_flops": tfl.value, "gemm_bytes": gb.value,
+            "tc_bytes": tb.value}
 
 
 def _stream(stream):

@@ -202,6 +202,8 @@ Launch add_gemm(std::vector<GJob> &all, const std::vector<GJob> &jobs_in, bool a
         all.push_back(j);
         L.cnt++;
         L.flops += 8.0 * j.m * j.n * j.k;
+        L.bytes += (g_plan_c64 ? 8.0 : 16.0) *
+                   ((double)j.m * j.k + (double)j.k * j.n + (double)j.m * j.n * ((j.flags & (GJ_SUB | GJ_ACC)) ? 2 : 1));
     }
     L.ntiles = tiles;
     return L;
@@ -636,7 +638,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                         g.B[z] = bbase ? inv[z] : pool[z];
                         g.C[z] = pool[z];
                     }
-                    launch_gemm<T>(g, ni, st, L.flops * ni);
+                    launch_gemm<T>(g, ni, st, L.flops * ni, L.bytes * ni);
                 };
                 gemm(S.panelL, 0, 1);   // L21 = A21 Uinv
                 gemm(S.panelU, 1, 0);   // U12 = Linv A12
@@ -673,7 +675,7 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
                     g.B[z] = finv[z];
                     g.C[z] = finv[z];
                 }
-                launch_gemm<T>(g, ni, st, L.flops * ni);
+                launch_gemm<T>(g, ni, st, L.flops * ni, L.bytes * ni);
             };
             for (size_t q = 0; q + 1 < F.linv.size(); q += 2) {
                 igemm(F.linv[q], false);
@@ -909,8 +911,10 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                         default: return (cx<T> *)h->W[z];
                     }
                 };
+                double by = 0.0;
                 for (int z = 0; z < ninst; ++z) {
                     const Launch &L = herm[z] ? o.LH : o.L;
+                    by += L.bytes;
                     g.jobs[z] = h->d_sjobs + L.off;
                     g.tmap[z] = L.tmoff >= 0 ? h->d_stmap + L.tmoff : nullptr;
                     g.njobs[z] = L.cnt;
@@ -920,7 +924,7 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                     g.C[z] = base(o.cbase, z);
                     fl += L.flops;
                 }
-                launch_gemm<T>(g, ninst, st, fl);
+                launch_gemm<T>(g, ninst, st, fl, by);
             } else {
                 RowArgs<T> r;
                 std::memset(&r, 0, sizeof(r));
@@ -1356,6 +1360,13 @@ int zolo_profile_end(void *stream, int64_t *launches, int64_t *gemm_launches, do
     if (gemm_ms) *gemm_ms = ms;
     if (gemm_flops) *gemm_flops = counters().gemm_flops;
     return rc;
+}
+
+int zolo_profile_bytes(double *gemm_bytes, double *tc_bytes) {
+    clear_error();
+    if (gemm_bytes) *gemm_bytes = counters().gemm_bytes;
+    if (tc_bytes) *tc_bytes = counters().tc_bytes;
+    return ZOLO_OK;
 }
 
 int zolo_profile_tc(int64_t *launches, double *ms, double *flops) {

@@ -12,6 +12,8 @@ struct Launch {
     int cnt = 0;         // jobs
     int ntiles = 0;      // CTAs
     double flops = 0.0;  // executed flops of a GEMM launch (8 m n k summed over jobs)
+    double bytes = 0.0;  // algorithmic bytes of its jobs: A, B read once, C written (and read if
+                         // accumulated), at the launch's element size
     int bm = 64;         // GEMM tile height of the launch
     int bn = 64;         // GEMM tile width
     bool tc = false;     // complex64 tensor-core kernel (bm = bn = 128)

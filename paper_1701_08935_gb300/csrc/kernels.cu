@@ -17,6 +17,7 @@ std::vector<cudaEvent_t> g_ev;       // start/stop pairs of profiled GEMM launch
 struct EvInfo {
     bool tc;                         // launched on the tensor-core kernel
     double flops;                    // executed flops of the launch
+    double bytes;                    // its algorithmic bytes (operands read once, C read if accumulated, written)
 };
 std::vector<EvInfo> g_ev_info;       // one per pair
 std::vector<cudaEvent_t> g_ev_pool;
@@ -47,6 +48,7 @@ double prof_collect_ms() {
             g_counters.tc_launches++;
             g_counters.tc_ms += t;
             g_counters.tc_flops += f.flops;
+            g_counters.tc_bytes += f.bytes;
         }
     }
     for (cudaEvent_t e : g_ev) g_ev_pool.push_back(e);
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(256) k_gemm_c64(GemmArgs<float> g) {
 }
 
 template <class T>
-void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops) {
+void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops, double bytes) {
     int mx = 0;
     for (int z = 0; z < ninst; ++z) mx = g.ntiles[z] > mx ? g.ntiles[z] : mx;
     if (mx == 0) return;
@@ -444,12 +446,13 @@ void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops)
         cudaEventRecord(e1, st);
         g_ev.push_back(e0);
         g_ev.push_back(e1);
-        g_ev_info.push_back({tc, flops});
+        g_ev_info.push_back({tc, flops, bytes});
     }
     g_counters.launches++;
     if (timed) {
         g_counters.gemm_launches++;
         g_counters.gemm_flops += flops;
+        g_counters.gemm_bytes += bytes;
     }
 }
 
@@ -1041,8 +1044,8 @@ void launch_transpose_sq(const EyeArgs<T> &g, int ninst, cudaStream_t st) {
 }
 
 // explicit instantiations
-template void launch_gemm<double>(const GemmArgs<double> &, int, cudaStream_t, double);
-template void launch_gemm<float>(const GemmArgs<float> &, int, cudaStream_t, double);
+template void launch_gemm<double>(const GemmArgs<double> &, int, cudaStream_t, double, double);
+template void launch_gemm<float>(const GemmArgs<float> &, int, cudaStream_t, double, double);
 template void launch_diag_lu<double>(const DiagArgs<double> &, int, cudaStream_t);
 template void launch_diag_lu<float>(const DiagArgs<float> &, int, cudaStream_t);
 template void launch_assemble<double>(const AsmArgs<double> &, int, cudaStream_t);

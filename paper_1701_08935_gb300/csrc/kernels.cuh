@@ -121,13 +121,16 @@ struct LaunchCounters {
     int64_t tc_launches = 0;       // the tensor-core subset of the timed GEMM launches,
     double tc_ms = 0.0;            // its summed device time (filled by prof_collect_ms)
     double tc_flops = 0.0;         // and its executed flops
+    double gemm_bytes = 0.0;       // algorithmic bytes of the timed GEMM launches
+    double tc_bytes = 0.0;         // ... of their tensor-core subset
 };
 LaunchCounters &counters();
 void count_launch(int64_t n = 1);
 void prof_set(int mask);          // bit 0: complex64 GEMMs, bit 1: complex128 GEMMs
 double prof_collect_ms();          // synchronises the recorded events, returns the summed time
                                    // (and adds the tensor-core share to counters().tc_*)
-template <class T> void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops = 0.0);
+template <class T>
+void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops = 0.0, double bytes = 0.0);
 // complex64 tcgen05 GEMM (tiles 128 x <= 128, bm = bn = 128 in the job tiling)
 void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st);
 // device status word of the tensor-core GEMM: 0, or ZOLO_ETIMEOUT after an expired
