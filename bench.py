@@ -639,6 +639,51 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_apply_case(args):
+    """Profiling case for ncu (no bench line): the workload's factorisation, then one
+    zolo_apply on a random real k-column block with at most --apply-steps GMRES steps (the
+    filter from the stored eigengaps, or from the workload's probe range when it has none),
+    that apply bracketed by cudaProfilerStart/Stop so that `ncu --profile-from-start off`
+    records the launches of those GMRES steps only."""
+    import torch
+    import paper_1701_08935_gb300 as Z
+    W = WORKLOADS[args.workload]
+    pen = build_pencil(W["recipe"])
+    if W["gaps"] is not None:
+        am, ap_, _, bm, bp, _ = W["gaps"]
+    else:
+        x0, x1 = W["probe"]
+        g = 0.01 * (x1 - x0)
+        am, ap_, bm, bp = x0 - g, x0, x1, x1 + g
+    flt = Z.Filter(am, ap_, bm, bp, *W["r"])
+    opts = Z.default_opts(grid=pen.dims, leaf_max=32, precision=Z.PREC_MIXED, gmres_tol=W["gmres_tol"],
+                          gmres_m_max=args.apply_steps)
+    fac = Z.Factor(pen.A, pen.B, flt, opts=opts)
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    X = torch.randn(pen.n, W["k"], generator=gen, dtype=torch.float64, device="cuda").to(torch.complex128)
+
+    def apply():
+        try:
+            return fac.apply(X)[1]
+        except Z.ZoloError as e:               # GMRES stopped at the step cap on purpose
+            if e.status != Z.ENOCONV:
+                raise
+            return fac.stats()
+
+    apply()                                      # schedules and workspaces
+    torch.cuda.synchronize()
+    Z.profile_begin(0)
+    t0 = time.perf_counter()
+    torch.cuda.profiler.start()
+    st = apply()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    p = Z.profile_end()
+    print(json.dumps({"case": "apply", "workload": args.workload, "n": pen.n, "k": W["k"],
+                      "gmres_steps": st["n_gmres"], "seconds": time.perf_counter() - t0,
+                      "launches": p["launches"], "t_factor_ms": fac.stats()["t_factor_ms"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -651,7 +696,14 @@ def main():
                     help="skip the one complex128 step of the same workload that follows the mixed measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--locate", action="store_true", help="locate the eigengaps by inertia counts and exit")
+    ap.add_argument("--case", default="bench", choices=["bench", "apply"],
+                    help="apply: profiling case for ncu (factorisation, then one zolo_apply of at most "
+                         "--apply-steps GMRES steps inside a profiler range); no bench line")
+    ap.add_argument("--apply-steps", type=int, default=3)
     args = ap.parse_args()
+    if args.case == "apply":
+        run_apply_case(args)
+        return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.locate:
