@@ -35,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 TOL = 1e-10
+TC_DRAM_OVER_ALG = 1.01       # ncu dram__bytes (read + write) / algorithmic bytes of k_gemm_tc solve products
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3    # SMs x FP32 lanes x 2 flop x max SM clock (GHz)
 
 # Workloads.  `gaps`: eigengaps (a-, a+, count below a, b-, b+, count below b) found once by
@@ -455,8 +456,15 @@ def roofline(Z, prec, gp, stp, flops_alg, t_step_ms):
             roof = {"bound": "tensor", "achieved": flops_tc / tc_s / 1e12, "peak": peak_t, "unit": "TFLOP/s",
                     "achieved_def": "algorithmic flops of the tensor-core GEMM jobs / their summed device time",
                     "peak_def": "of measured: bf16_tflops_sustained x 1.1/2.25 (nominal TF32/bf16) / 3 (3xTF32)"}
+        # DRAM traffic per launch: the algorithmic bytes of an average launch of this step times
+        # the DRAM / algorithmic ratio ncu measured on the same kernel's top-level solve products
+        # of the 48^3 case of this recipe (89.4 MB read + written for 88.5 MB algorithmic)
+        tc_launches = max(1, gp["tc_launches"])
         roof.update({"kernel": "k_gemm_tc (tcgen05.mma kind::tf32, 3xTF32 complex64 front / solve products)",
-                     "traffic": None, "t_roof_over_t": max(t_flops, t_bytes) / tc_s,
+                     "traffic": gp["tc_bytes"] / tc_launches * TC_DRAM_OVER_ALG,
+                     "traffic_def": "bytes per launch: algorithmic bytes per launch x DRAM/algorithmic ratio "
+                                    f"{TC_DRAM_OVER_ALG} measured by ncu on the 48^3 case (scaled by units)",
+                     "t_roof_over_t": max(t_flops, t_bytes) / tc_s,
                      "tensor_view": {"achieved_tflops": flops_tc / tc_s / 1e12, "peak_tflops": peak_t,
                                      "frac": flops_tc / tc_s / 1e12 / peak_t},
                      "hbm_view": {"achieved_gbs": gp["tc_bytes"] / tc_s / 1e9, "peak_gbs": hbm,
