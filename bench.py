@@ -680,16 +680,23 @@ def run_apply_case(args):
 
     apply()                                      # schedules and workspaces
     torch.cuda.synchronize()
-    Z.profile_begin(0)
+    Z.profile_begin(1 if args.gemm_events else 0)
     t0 = time.perf_counter()
     torch.cuda.profiler.start()
     st = apply()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     p = Z.profile_end()
-    print(json.dumps({"case": "apply", "workload": args.workload, "n": pen.n, "k": W["k"],
-                      "gmres_steps": st["n_gmres"], "seconds": time.perf_counter() - t0,
-                      "launches": p["launches"], "t_factor_ms": fac.stats()["t_factor_ms"]}))
+    out = {"case": "apply", "workload": args.workload, "n": pen.n, "k": W["k"], "gmres_steps": st["n_gmres"],
+           "seconds": time.perf_counter() - t0, "launches": p["launches"],
+           "t_factor_ms": fac.stats()["t_factor_ms"]}
+    if args.gemm_events:                         # device time of every GEMM launch, by engine
+        out.update({"tc_ms": p["tc_ms"], "tc_launches": p["tc_launches"],
+                    "tc_gbs": p["tc_bytes"] / (p["tc_ms"] * 1e6) if p["tc_ms"] > 0 else None,
+                    "fma_ms": p["gemm_ms"] - p["tc_ms"],
+                    "fma_gbs": (p["gemm_bytes"] - p["tc_bytes"]) / ((p["gemm_ms"] - p["tc_ms"]) * 1e6)
+                    if p["gemm_ms"] > p["tc_ms"] else None})
+    print(json.dumps(out))
 
 
 def main():
@@ -708,6 +715,9 @@ def main():
                     help="apply: profiling case for ncu (factorisation, then one zolo_apply of at most "
                          "--apply-steps GMRES steps inside a profiler range); no bench line")
     ap.add_argument("--apply-steps", type=int, default=3)
+    ap.add_argument("--gemm-events", action="store_true",
+                    help="--case apply: time every GEMM launch with CUDA events and report the device "
+                         "time and algorithmic GB/s of each engine")
     args = ap.parse_args()
     if args.case == "apply":
         run_apply_case(args)
