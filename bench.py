@@ -18,6 +18,8 @@ R(B^-1 A) x = R(lam) x on sampled pairs); value is 0 when a check fails.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
                   [--workload lap96|peierls64|lap48] [--no-fp64-compare] [--locate]
   python bench.py --impl reference      # the CPU oracle on a bounded sample
+  python bench.py --case ex1 [--precision fp64]   # Example 1 of Section 3.1 (Table 1), N = 12^3..52^3
+  python bench.py --case apply [--apply-steps M] [--gemm-events]   # profiling case: one zolo_apply
 """
 import argparse
 import json
@@ -699,6 +701,113 @@ def run_apply_case(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------------------- Example 1
+# Section 3.1, Example 1 and Table 1: H = -1/2 Laplacian + three Gaussian wells on the unit
+# cube (Dirichlet, 7-point stencil, n^3 grid), B = I; the smallest 88 eigenpairs with
+# a- = -inf, a+ = lam_1, b- = lam_88, b+ = lam_89 (the true eigenvalues as input), r = (4, 4),
+# subspace dimension 89, tolerance 1e-8, five runs with different random starting blocks.
+# As in the paper, each size takes the first potential (seed 1, 2, ...) whose relative
+# eigengap delta = (lam_89 - lam_88) / (lam_88 - lam_1) lies in [1e-4, 1e-3].
+# EX1[n] = (seed, lam_1, lam_88, lam_89, lam_90), written by `python bench.py --case ex1
+# --locate` (scipy shift-invert Lanczos on the host); every run re-checks the numbering with
+# FP64 inertia counts on the GPU.
+EX1_SIDES = (12, 20, 28, 36, 44, 52)
+EX1 = {
+    12: (2, 14.612729459959986, 172.7309911421261, 172.75770268084756, 172.75920261739648),
+    20: (2, 14.65706744305735, 190.39212389007469, 190.41855179751266, 190.4201059133565),
+    28: (2, 14.670188659299793, 195.91096737692354, 195.93737714586064, 195.93893168837795),
+    36: (2, 14.675770585067744, 198.3004808583303, 198.32688511184614, 198.32843913088578),
+    44: (2, 14.678651403448859, 199.54355030384795, 199.56994969775207, 199.57150544401608),
+    52: (2, 14.6803295458486, 200.27077193992415, 200.29716553467694, 200.2987250217176),
+}
+# Table 1 of the paper (MATLAB, one CPU): N -> (delta, n_gmres, n_solv, T_fact, T_iter, T_total) in s.
+EX1_PAPER = {1728: (8.6e-4, 14, 4984, 0.28, 2.2, 2.6), 8000: (5.1e-4, 16, 5625, 1.6, 14.0, 16.0),
+             21952: (4.3e-4, 15, 5340, 7.9, 45.0, 52.0), 46656: (6.6e-4, 15, 5340, 29.0, 110.0, 140.0),
+             85184: (2.4e-4, 16, 5696, 83.0, 240.0, 330.0), 140608: (1.6e-4, 17, 6052, 220.0, 490.0, 710.0)}
+
+
+def ex1_locate(sides, max_seed=60):
+    """Seed search of Example 1 on the host: the 92 smallest eigenvalues by scipy's
+    shift-invert Lanczos (sigma = 0 lies below the spectrum: -1/2 Laplacian >= 3 pi^2 / 2 > 3 >= -V)."""
+    import scipy.sparse.linalg as sla
+    import synth
+    for n in sides:
+        for seed in range(1, max_seed + 1):
+            pen = synth.hamiltonian_wells(n, seed)
+            w = np.sort(sla.eigsh(pen.A, k=92, sigma=0.0, which="LM", return_eigenvectors=False))
+            delta = (w[88] - w[87]) / (w[87] - w[0])
+            print(f"[ex1 locate] n={n} seed={seed} delta={delta:.3e}", file=sys.stderr, flush=True)
+            if 1e-4 <= delta <= 1e-3:
+                print(f"    {n}: ({seed}, {float(w[0])!r}, {float(w[87])!r}, {float(w[88])!r}, {float(w[89])!r}),",
+                      flush=True)
+                break
+
+
+def run_ex1_case(args):
+    """Example 1 at every side of EX1_SIDES (those stored in EX1): five runs each of
+    refactor + Algorithm 1, T_fact and T_iter by wall clock around the synchronised calls,
+    means as in Table 1, and the fitted exponents of T_fact and T_iter in N."""
+    import torch
+    import paper_1701_08935_gb300 as Z
+    import synth
+    prec = Z.PREC_MIXED if args.precision == "mixed" else Z.PREC_FP64
+    sides = [int(x) for x in args.ex1_sides.split(",")] if args.ex1_sides else list(EX1_SIDES)
+    rows = []
+    for n in sides:
+        if n not in EX1:
+            print(f"[ex1] side {n} has no stored potential; run --case ex1 --locate", file=sys.stderr)
+            continue
+        seed, l1, l88, l89, l90 = EX1[n]
+        pen = synth.hamiltonian_wells(n, seed)
+        iopts = Z.default_opts(grid=pen.dims, leaf_max=32)
+        sym = Z.Symbolic(pen.A, pen.B, iopts)
+        c = [int(v) for v in _counts(Z, pen, sym, iopts, [l1 - 1e-6 * (l88 - l1), 0.5 * (l88 + l89),
+                                                          0.5 * (l89 + l90)])]
+        if c != [0, 88, 89]:
+            raise RuntimeError(f"Example 1 at n={n}: inertia counts {c}, expected [0, 88, 89]")
+        flt = Z.Filter(-math.inf, l1, l88, l89, 4, 4)
+        opts = Z.default_opts(grid=pen.dims, leaf_max=32, precision=prec, tol=1e-8, gmres_tol=1e-12,
+                              gmres_m_max=100, n_iter_max=1, k=89, refine_max=40, verbose=args.verbose)
+        fac = Z.Factor(pen.A, pen.B, flt, sym=sym, opts=opts)
+        a, b = l1 - 0.5 * (l88 - l1), 0.5 * (l88 + l89)
+        runs = []
+        for run in range(args.ex1_runs + 1):              # run 0 warms up (schedules, workspaces)
+            X0 = torch.from_numpy(synth.random_block(pen.n, 89, 100 * n + run, complex_=False)).to(
+                torch.complex128).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fac.refactor()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ev, V, res, st, rc = fac.eigs(a, b, 89, X0=X0, cap=89)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            found = int(np.sum((ev > a) & (ev < b) & (res <= 1e-8)))
+            if run > 0:
+                runs.append(dict(t_fact=t1 - t0, t_iter=t2 - t1, relerr=st["relerr"], n_iter=st["n_iter"],
+                                 n_gmres=st["n_gmres"] / max(1, st["n_iter"]), n_solv=st["n_solv"],
+                                 found=found, rc=rc, max_resid=float(np.max(res)) if len(res) else None))
+            del V
+        mean = {k: float(np.mean([r[k] for r in runs])) for k in ("t_fact", "t_iter", "relerr", "n_iter",
+                                                                   "n_gmres", "n_solv", "found")}
+        mean["t_total"] = mean["t_fact"] + mean["t_iter"]
+        row = {"N": pen.n, "side": n, "seed": seed, "delta": (l89 - l88) / (l88 - l1), "r": [4, 4], "n_ss": 89,
+               **{k: float(f"{v:.4g}") for k, v in mean.items()}, "rc": [r["rc"] for r in runs],
+               "t_fact_range": [min(r["t_fact"] for r in runs), max(r["t_fact"] for r in runs)],
+               "t_iter_range": [min(r["t_iter"] for r in runs), max(r["t_iter"] for r in runs)],
+               "all_88": all(r["found"] == 88 for r in runs), "max_resid": max((r["max_resid"] for r in runs if r["max_resid"] is not None), default=None),
+               "paper": EX1_PAPER.get(pen.n)}
+        rows.append(row)
+        print(json.dumps({"case": "ex1", **row}), flush=True)
+        del fac, sym
+        torch.cuda.empty_cache()
+    if len(rows) >= 2:
+        lN = np.log([r["N"] for r in rows])
+        fit = {k: float(np.polyfit(lN, np.log([r[k] for r in rows]), 1)[0]) for k in ("t_fact", "t_iter")}
+        print(json.dumps({"case": "ex1", "precision": args.precision, "exponent_t_fact": fit["t_fact"],
+                          "exponent_t_iter": fit["t_iter"], "sizes": [r["N"] for r in rows]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -711,9 +820,13 @@ def main():
                     help="skip the one complex128 step of the same workload that follows the mixed measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--locate", action="store_true", help="locate the eigengaps by inertia counts and exit")
-    ap.add_argument("--case", default="bench", choices=["bench", "apply"],
+    ap.add_argument("--case", default="bench", choices=["bench", "apply", "ex1"],
                     help="apply: profiling case for ncu (factorisation, then one zolo_apply of at most "
-                         "--apply-steps GMRES steps inside a profiler range); no bench line")
+                         "--apply-steps GMRES steps inside a profiler range); ex1: Example 1 of "
+                         "Section 3.1 (Table 1) at every stored side; no bench line")
+    ap.add_argument("--ex1-sides", default="", help="--case ex1: comma-separated grid sides")
+    ap.add_argument("--ex1-runs", type=int, default=5, help="--case ex1: timed runs per side")
+    ap.add_argument("--verbose", type=int, default=0, help="the library's per-iteration log (stderr)")
     ap.add_argument("--apply-steps", type=int, default=3)
     ap.add_argument("--gemm-events", action="store_true",
                     help="--case apply: time every GEMM launch with CUDA events and report the device "
@@ -721,6 +834,12 @@ def main():
     args = ap.parse_args()
     if args.case == "apply":
         run_apply_case(args)
+        return
+    if args.case == "ex1":
+        if args.locate:
+            ex1_locate([int(x) for x in args.ex1_sides.split(",")] if args.ex1_sides else EX1_SIDES)
+        else:
+            run_ex1_case(args)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

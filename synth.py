@@ -156,6 +156,32 @@ def pencil_3d_peierls(n=64, seed=2, theta=0.05, wells=32):
                   f"seed={seed}; theta={theta}; {wells} wells d~U[-5,0] w~U[1,4]; B=M1^(x3)")
 
 
+def hamiltonian_wells(n, seed, wells=3, radius=0.2):
+    """The 3D Hamiltonian H = -1/2 Laplacian + V of Section 3.1 (Example 1) on the unit cube
+    with a Dirichlet boundary: n interior points per axis at x_i = i h, i = 1..n,
+    h = 1/(n+1), the 7-point finite-difference Laplacian (so -1/2 Laplacian has 3/h^2 on
+    the diagonal and -1/(2h^2) on each neighbour), and V = sum of ``wells`` Gaussian wells
+    -d exp(-|r - c|^2 / (2 radius^2)) with depth d uniform in (0, 1] and centre c uniform
+    in [0, 1)^3.  B = I.  Returned as a real pencil on the (n, n, n) grid."""
+    rng = np.random.default_rng(seed)
+    dims = (n, n, n)
+    h = 1.0 / (n + 1)
+    d = 1.0 - rng.uniform(0.0, 1.0, size=wells)          # (0, 1]
+    c = rng.uniform(0.0, 1.0, size=(wells, 3))
+    idx = np.arange(n ** 3)
+    x = (idx % n + 1) * h
+    y = ((idx // n) % n + 1) * h
+    z = (idx // (n * n) + 1) * h
+    V = np.zeros(n ** 3)
+    for t in range(wells):
+        r2 = (x - c[t, 0]) ** 2 + (y - c[t, 1]) ** 2 + (z - c[t, 2]) ** 2
+        V -= d[t] * np.exp(-r2 / (2.0 * radius ** 2))
+    A = (laplacian(dims) * (0.5 / h ** 2) + sp.diags(V)).tocsr()
+    B = _eye(n ** 3)
+    return Pencil(A, B, dims, f"ham3d_{n}^3_wells",
+                  f"seed={seed}; -1/2 Laplacian (h=1/{n + 1}) + {wells} wells d~U(0,1] radius {radius}; B=I")
+
+
 def random_block(n, k, seed, complex_=True):
     """N x k starting block with standard normal entries (complex: (N(0,1)+iN(0,1))/sqrt 2),
     row-major (k fastest)."""
