@@ -34,7 +34,9 @@ cudaEvent_t get_event() {
 }  // namespace
 
 LaunchCounters &counters() { return g_counters; }
-void count_launch(int64_t n) { g_counters.launches += n; }
+// Launch counts come from every calling thread: relaxed atomic increments (the profiling
+// fields below are process-wide and documented as not thread-safe).
+void count_launch(int64_t n) { __atomic_fetch_add(&g_counters.launches, n, __ATOMIC_RELAXED); }
 void prof_set(int mask) { g_prof = mask; }
 double prof_collect_ms() {
     double ms = 0.0;
@@ -448,7 +450,7 @@ void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops,
         g_ev.push_back(e1);
         g_ev_info.push_back({tc, flops, bytes});
     }
-    g_counters.launches++;
+    count_launch();
     if (timed) {
         g_counters.gemm_launches++;
         g_counters.gemm_flops += flops;
@@ -539,14 +541,16 @@ template <class T>
 void launch_diag_lu(const DiagArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.njobs == 0) return;
     const size_t smem = 2 * NB * NB * sizeof(c128);
-    static bool attr = false;
-    if (!attr) {
+    static bool attr_set[64] = {};                  // per device: the kernel's shared-memory opt-in
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
         cudaFuncSetAttribute(k_diag_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+        attr_set[dev] = true;
     }
     dim3 grid(g.njobs, 1, ninst);
     k_diag_lu<T><<<grid, 256, smem, st>>>(g);
-    g_counters.launches++;
+    count_launch();
 }
 
 // ============================================================== assembly
@@ -567,7 +571,7 @@ void launch_assemble(const AsmArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.count == 0) return;
     dim3 grid((unsigned)((g.count + 255) / 256), 1, ninst);
     k_assemble<T><<<grid, 256, 0, st>>>(g);
-    g_counters.launches++;
+    count_launch();
 }
 
 // ============================================================== matrix extend-add
@@ -611,7 +615,7 @@ void launch_extend_add(const EaddArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.ntiles == 0) return;
     dim3 grid(g.ntiles, 1, ninst);
     k_extend_add<T><<<grid, 256, 0, st>>>(g);
-    g_counters.launches++;
+    count_launch();
 }
 
 // ============================================================== row moves
@@ -673,7 +677,7 @@ void launch_rows(const RowArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.ntiles == 0) return;
     dim3 grid(g.ntiles, 1, ninst);
     k_rows<T><<<grid, 256, 0, st>>>(g);
-    g_counters.launches++;
+    count_launch();
 }
 
 // ============================================================== identity starts
@@ -698,7 +702,7 @@ void launch_eye(const EyeArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.ntiles == 0) return;
     dim3 grid(g.ntiles, 1, ninst);
     k_eye_blocks<T><<<grid, 256, 0, st>>>(g);
-    g_counters.launches++;
+    count_launch();
 }
 
 // ============================================================== SpMM
@@ -752,7 +756,7 @@ void launch_spmm(const DevCSR &M, int64_t k, const c128 *X, int64_t ldx, c128 *Y
         k_spmm_real<<<grid, 256, 0, st>>>(M.rp, M.ci, M.vr, M.n, (int)k, X, ldx, Y, ldy, s, acc ? 1 : 0);
     else
         k_spmm<<<grid, 256, 0, st>>>(M.rp, M.ci, M.v, M.n, (int)k, X, ldx, Y, ldy, s, acc ? 1 : 0);
-    g_counters.launches++;
+    count_launch();
 }
 
 // Refinement residuals of all instances in one pass over the rows of A and M
@@ -795,7 +799,7 @@ __global__ void __launch_bounds__(256) k_refine_resid(DevCSR A, DevCSR M, ResidA
 void launch_refine_resid(const DevCSR &A, const DevCSR &M, const ResidArgs &r, cudaStream_t st) {
     if (A.n == 0 || r.k == 0 || r.ninst == 0) return;
     k_refine_resid<<<(unsigned)((A.n + 7) / 8), 256, 0, st>>>(A, M, r);
-    g_counters.launches++;
+    count_launch();
 }
 
 // Double-float variant: the sums over the rows of A and M, sigma M x and b - A x + sigma M x
@@ -866,7 +870,7 @@ __global__ void __launch_bounds__(256) k_refine_resid_df(DevCSR A, DevCSR M, Res
 void launch_refine_resid_df(const DevCSR &A, const DevCSR &M, const ResidDfArgs &r, cudaStream_t st) {
     if (A.n == 0 || r.k == 0 || r.ninst == 0) return;
     k_refine_resid_df<<<(unsigned)((A.n + 7) / 8), 256, 0, st>>>(A, M, r);
-    g_counters.launches++;
+    count_launch();
 }
 
 __global__ void __launch_bounds__(256) k_spmm_df(DevCSR M, int k, const float2 *__restrict__ Xs,
@@ -903,7 +907,7 @@ __global__ void __launch_bounds__(256) k_spmm_df(DevCSR M, int k, const float2 *
 void launch_spmm_df(const DevCSR &M, int64_t k, const float2 *Xs, c128 *Y, cudaStream_t st) {
     if (M.n == 0 || k == 0) return;
     k_spmm_df<<<(unsigned)((M.n + 7) / 8), 256, 0, st>>>(M, (int)k, Xs, Y);
-    g_counters.launches++;
+    count_launch();
 }
 
 __global__ void k_split_df(int64_t n, int k, const c128 *__restrict__ X, int64_t ldx, float4 *__restrict__ Xs) {
@@ -921,7 +925,7 @@ void launch_split_df(int64_t n, int64_t k, const c128 *X, int64_t ldx, float4 *X
     const int64_t tot = n * k;
     if (tot == 0) return;
     k_split_df<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, (int)k, X, ldx, Xs);
-    g_counters.launches++;
+    count_launch();
 }
 
 // ============================================================== elementwise
@@ -940,7 +944,7 @@ void launch_lincomb(const LinArgs &a, cudaStream_t st) {
     const int64_t tot = a.n * a.k;
     if (tot == 0) return;
     k_lincomb<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a);
-    g_counters.launches++;
+    count_launch();
 }
 
 // ============================================================== column norms
@@ -997,7 +1001,7 @@ void launch_colnorm2(int64_t n, int64_t k, const c128 *X, int64_t ldx, double *o
     if (k <= 0) return;
     k_colnorm_part<<<COLNORM_PARTS, 256, 0, st>>>(n, (int)k, X, ldx, part, imag_only ? 1 : 0);
     k_colnorm_sum<<<(unsigned)((k + 7) / 8), 256, 0, st>>>((int)k, COLNORM_PARTS, part, out);
-    g_counters.launches += 2;
+    count_launch(2);
 }
 
 // ============================================================== square transposes
@@ -1040,7 +1044,7 @@ void launch_transpose_sq(const EyeArgs<T> &g, int ninst, cudaStream_t st) {
     if (g.ntiles == 0) return;
     dim3 grid(g.ntiles, 1, ninst);
     k_transpose_sq<T><<<grid, 256, 0, st>>>(g);
-    g_counters.launches++;
+    count_launch();
 }
 
 // explicit instantiations
