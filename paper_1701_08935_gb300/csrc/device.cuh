@@ -50,9 +50,24 @@ struct GJob {
     int32_t tm;         // tiles along m
     int32_t flags;      // GJ_CONJA | GJ_CONJB | GJ_SUB | GJ_ACC
     int32_t ks;         // split of the kk extent over ks CTAs (results added atomically)
+    int64_t ps;         // GJ_PRESPLIT: float offset of A's pre-split tensor-core planes
 };
-// GJ_SUB: C -= AB, GJ_ACC: C += AB, neither: C = AB (never split)
-enum { GJ_CONJA = 1, GJ_CONJB = 2, GJ_SUB = 4, GJ_ACC = 8 };
+// GJ_SUB: C -= AB, GJ_ACC: C += AB, neither: C = AB (never split).  GJ_PRESPLIT: A is also
+// stored pre-split (see PJob); the tensor-core kernel loads those planes instead of A.
+enum { GJ_CONJA = 1, GJ_CONJB = 2, GJ_SUB = 4, GJ_ACC = 8, GJ_PRESPLIT = 16 };
+
+// One operand of the block solves (column-major, rows contiguous) kept pre-split for the
+// tensor cores: per 128-row tile rt and k-step ks of 8, a 16 KB block at float offset
+// ps + (rt * ceil(k / 8) + ks) * 4096 holding the four TF32 planes (re hi, re lo, im hi,
+// im lo) of that 128 x 8 tile in the canonical no-swizzle K-major layout, zero-padded.
+struct PJob {
+    int64_t a;          // element offset of the operand's (0,0) entry
+    int64_t ps;         // float offset of its blocks in the pre-split buffer
+    int64_t blk0;       // its first block in the build launch
+    int32_t acs;        // column stride
+    int32_t m, k;       // rows, inner extent
+    int32_t base;       // 0: front pool, 1: pivot-block inverses
+};
 
 // A diagonal block of a front: LU in place (FP64), inverses of L and U stored.
 struct DJob {

@@ -700,6 +700,101 @@ template <class T> int run_factor(zolo_factor_s *h, cudaStream_t st) {
 
 }  // namespace
 
+// Pre-split solve operands (mixed precision): L_pp^-1, U_pp^-1, L_up and U_pu of every front
+// whose operand has >= 128 rows and an inner extent >= 64 -- the products the tensor-core
+// kernel takes -- get a copy as TF32 planes (16 bytes per element against 8, see PJob).  The
+// copies are optional: when they would take more than half of the free device memory, or the
+// allocation fails, the solves convert A on the fly as before.
+static int setup_presplit(zolo_factor_s *h) {
+    const zolo_symbolic_s &S = h->sym;
+    const int nn = S.nnodes;
+    h->f_ps.assign(4 * (size_t)nn, -1);
+    std::vector<PJob> pj;
+    int64_t fl = 0, blk = 0;
+    auto add = [&](int s, int kind, int64_t a, int acs, int m, int k, int base) {
+        if (m < 128 || k < 64) return;
+        PJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.a = a;
+        j.ps = fl;
+        j.blk0 = blk;
+        j.acs = acs;
+        j.m = m;
+        j.k = k;
+        j.base = base;
+        const int64_t nb = (int64_t)((m + 127) / 128) * ((k + 7) / 8);
+        h->f_ps[4 * (size_t)s + kind] = fl;
+        fl += nb * 4096;
+        blk += nb;
+        pj.push_back(j);
+    };
+    for (int s = 0; s < nn; ++s) {
+        const int np = S.npiv[s], nu = S.nu(s), nf = S.nf(s);
+        const int64_t X = h->f_finv[s], o = h->f_off[s];
+        add(s, 0, X, np, np, np, 1);                            // L_pp^-1 (column-major)
+        add(s, 1, X + (int64_t)np * np, np, np, np, 1);         // U_pp^-1
+        add(s, 2, o + np, nf, nu, np, 0);                       // L_up
+        add(s, 3, o + (int64_t)np * nf, nf, np, nu, 0);         // U_pu
+    }
+    auto disable = [&]() {
+        h->f_ps.assign(4 * (size_t)nn, -1);
+        h->n_psjobs = 0;
+        h->ps_floats = h->ps_blocks = 0;
+    };
+    if (pj.empty()) {
+        disable();
+        return ZOLO_OK;
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        disable();
+        return ZOLO_OK;
+    }
+    const double need = (double)fl * 4.0 * h->r1 + (double)pj.size() * sizeof(PJob);
+    if (need > 0.5 * (double)free_b || blk > 0x7fffffffLL) {
+        disable();
+        return ZOLO_OK;
+    }
+    for (int j = 0; j < h->r1; ++j) {
+        if (dev_alloc(h, (size_t)fl * sizeof(float), &h->presplit[j])) {
+            for (int q = 0; q < j; ++q) {
+                dev_free(h, h->presplit[q]);
+                h->presplit[q] = nullptr;
+            }
+            clear_error();
+            disable();
+            return ZOLO_OK;
+        }
+    }
+    int rc = dev_alloc(h, pj.size() * sizeof(PJob), (void **)&h->d_psjobs);
+    if (!rc) rc = cuda_check(cudaMemcpy(h->d_psjobs, pj.data(), pj.size() * sizeof(PJob), cudaMemcpyHostToDevice),
+                             "presplit jobs");
+    if (rc) return rc;
+    h->n_psjobs = (int)pj.size();
+    h->ps_floats = fl;
+    h->ps_blocks = blk;
+    return ZOLO_OK;
+}
+
+// the pre-split planes of the current factors (after every factorisation)
+static void build_presplit(zolo_factor_s *h, cudaStream_t st) {
+    if (h->n_psjobs == 0) return;
+    for (int p0 = 0; p0 < h->r1; p0 += MAX_INST) {
+        const int ni = std::min(MAX_INST, h->r1 - p0);
+        PresplitArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.jobs = h->d_psjobs;
+        a.njobs = h->n_psjobs;
+        for (int z = 0; z < ni; ++z) {
+            a.pool[z] = (const c64 *)h->pool[p0 + z];
+            a.finv[z] = (const c64 *)h->finv[p0 + z];
+            a.out[z] = (float *)h->presplit[p0 + z];
+        }
+        launch_presplit(a, h->ps_blocks, ni, st);
+    }
+}
+
 int factor_numeric(zolo_factor_s *h, cudaStream_t st) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -708,6 +803,7 @@ int factor_numeric(zolo_factor_s *h, cudaStream_t st) {
     h->stats.solve_cols = 0;                       // per-factorisation counters
     h->stats.n_refine_max = 0;
     int rc = (h->prec == ZOLO_PREC_MIXED) ? run_factor<float>(h, st) : run_factor<double>(h, st);
+    if (!rc && h->prec == ZOLO_PREC_MIXED) build_presplit(h, st);
     cudaEventRecord(e1, st);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "factor");
     float ms = 0.f;
@@ -727,6 +823,16 @@ int factor_numeric(zolo_factor_s *h, cudaStream_t st) {
     h->stats.min_pivot = m;
     if (err) return set_error(ZOLO_ESINGULAR, "zero or non-finite pivot in a front");
     return check_tc_status();
+}
+
+// a non-Hermitian solve job of front s whose operand `kind` (PJob order) is pre-split
+static GJob presplit_job(const zolo_factor_s *h, int s, int kind, GJob j) {
+    const size_t i = 4 * (size_t)s + kind;
+    if (i < h->f_ps.size() && h->f_ps[i] >= 0) {
+        j.flags |= GJ_PRESPLIT;
+        j.ps = h->f_ps[i];
+    }
+    return j;
 }
 
 // ---- solve schedule for a block width k
@@ -803,10 +909,10 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
             const int64_t wp = h->f_wrow[s] * k, wu = (h->f_wrow[s] + np) * k, y = (int64_t)S.first[s] * k;
             // Y starts zeroed (the whole pivot-row block is cleared per solve): accumulate
             // Linv and Uinv are stored column-major (transposed in place after they are formed)
-            yN.push_back(make_job(X, 1, np, wp, K, 1, y, K, 1, np, K, np, GJ_ACC));                     // Linv
+            yN.push_back(presplit_job(h, s, 0, make_job(X, 1, np, wp, K, 1, y, K, 1, np, K, np, GJ_ACC)));  // Linv
             yH.push_back(make_job(X + (int64_t)np * np, np, 1, wp, K, 1, y, K, 1, np, K, np,
                                   GJ_ACC | GJ_CONJA));                                                   // Uinv^H
-            uN.push_back(make_job(o + np, 1, nf, y, K, 1, wu, K, 1, nu, K, np, GJ_SUB));                 // L_up
+            uN.push_back(presplit_job(h, s, 2, make_job(o + np, 1, nf, y, K, 1, wu, K, 1, nu, K, np, GJ_SUB)));  // L_up
             uH.push_back(make_job(o + (int64_t)np * nf, nf, 1, y, K, 1, wu, K, 1, nu, K, np, GJ_SUB | GJ_CONJA));
         }
         h->fwd.push_back(gemm_op(yN, yH, BK_INVFULL, BK_W, BK_YP));
@@ -822,10 +928,12 @@ int ensure_solve_schedule(zolo_factor_s *h, int64_t k) {
             const int64_t X = h->f_finv[s], o = h->f_off[s];
             const int64_t wp = h->f_wrow[s] * k, wu = (h->f_wrow[s] + np) * k, y = (int64_t)S.first[s] * k;
             if (nu > 0) g.push_back(rjob(0, wu, h->f_rows[s] + np, nu));
-            aN.push_back(make_job(o + (int64_t)np * nf, 1, nf, wu, K, 1, y, K, 1, np, K, nu, GJ_SUB));  // U_pu
+            aN.push_back(presplit_job(h, s, 3, make_job(o + (int64_t)np * nf, 1, nf, wu, K, 1, y, K, 1, np, K, nu,
+                                                        GJ_SUB)));                                        // U_pu
             aH.push_back(make_job(o + np, nf, 1, wu, K, 1, y, K, 1, np, K, nu, GJ_SUB | GJ_CONJA));      // L_up^H
             // W_p is cleared first (ROW_ZERO), then accumulated into
-            xN.push_back(make_job(X + (int64_t)np * np, 1, np, y, K, 1, wp, K, 1, np, K, np, GJ_ACC));   // Uinv
+            xN.push_back(presplit_job(h, s, 1, make_job(X + (int64_t)np * np, 1, np, y, K, 1, wp, K, 1, np, K, np,
+                                                        GJ_ACC)));                                        // Uinv
             xH.push_back(make_job(X, np, 1, y, K, 1, wp, K, 1, np, K, np, GJ_ACC | GJ_CONJA));           // Linv^H
             sc.push_back(rjob(wp, 0, h->f_rows[s], np));
             zr.push_back(rjob(0, wp, 0, np));
@@ -922,6 +1030,7 @@ int run_solve(zolo_factor_s *h, int ninst, const int *pole, const int *herm, int
                     g.A[z] = base(o.abase, z);
                     g.B[z] = base(o.bbase, z);
                     g.C[z] = base(o.cbase, z);
+                    g.ps[z] = (const float *)h->presplit[pole[z]];
                     fl += L.flops;
                 }
                 launch_gemm<T>(g, ninst, st, fl, by);
@@ -1276,6 +1385,7 @@ static int factor_create(const zolo_csr *A, const zolo_csr *B, const zolo_filter
         if (!rc) rc = dev_alloc(h, std::max<int64_t>(1, h->inv_elems) * eb, &h->inv[j]);
         if (!rc) rc = dev_alloc(h, (count_neg ? 1 : std::max<int64_t>(1, h->finv_elems)) * eb, &h->finv[j]);
     }
+    if (!rc && h->prec == ZOLO_PREC_MIXED && !count_neg) rc = setup_presplit(h);
     h->stats.flops_factor = h->sym.info.flops_lu * h->r1;
     h->stats.flops_solve = 16.0 * (double)h->sym.info.nnz_factor;     // fwd + bwd, complex, per column
     if (!rc) rc = factor_numeric(h, stream);

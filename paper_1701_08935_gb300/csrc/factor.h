@@ -78,6 +78,14 @@ struct zolo_factor_s {
     void *inv[ZOLO_MAX_R] = {};                    // per pole: diagonal-block inverses (T)
     void *finv[ZOLO_MAX_R] = {};                   // per pole: full pivot-block inverses, L then U
                                                    // (np x np each, column-major once formed)
+    // pre-split solve operands (MIXED): per front, the float offsets of the tensor-core planes
+    // of its [Linv, Uinv, L_up, U_pu] (-1: none), one buffer per pole, rebuilt by every
+    // factorisation
+    std::vector<int64_t> f_ps;
+    int64_t ps_floats = 0, ps_blocks = 0;
+    int n_psjobs = 0;
+    void *presplit[ZOLO_MAX_R] = {};
+    zolo::PJob *d_psjobs = nullptr;
     int32_t *d_rows = nullptr, *d_rel = nullptr;
     int64_t *d_asm = nullptr;                      // [srcA | dstA | srcB | dstB]
     int64_t nA_asm = 0, nB_asm = 0;

@@ -19,6 +19,12 @@
 // ~5-10x less accurate than with FP32 FMAs (~1e-6 relative at k = 64); the FP64 refinement of
 // every mixed-precision solve absorbs this.
 //
+// Pre-split operands: a job flagged GJ_PRESPLIT (the block solves' column-major factor
+// operands, mixed precision) has its A already stored as the four TF32 planes of every
+// 128 x 8 stage (16 KB blocks, k_presplit below, built once per factorisation).  Its A stage
+// is then one bulk copy straight into the MMA stage (thread 0 adds the bytes to the stage's
+// "full" mbarrier), and the converters only split B: no A staging, no A conversion.
+//
 // Tiles: one CTA per 128 x w tile of C, w <= 128 columns chosen per job so that the
 // ceil(n / 128) column tiles have equal width (a multiple of 16); 256 tensor-memory columns
 // per CTA.
@@ -63,8 +69,10 @@ template <int WMAX> struct TcPlan {
     static constexpr int RAW_A = TC_BM * TC_BK * 8;                   // raw complex64 A stage (8 KB)
     static constexpr int RAW_STAGE = RAW_A + WMAX * TC_BK * 8;
     static constexpr int CTAS = 2;                                    // CTAs per SM
-    static constexpr int NB = 2;                                      // MMA stages
-    static constexpr int P = WMAX <= 32 ? 6 : (WMAX <= 64 ? 4 : 3);   // raw stages in the ring
+    // MMA stages (a pre-split A stage is in flight only while its MMA stage waits: three of
+    // them for the 32-wide solve tiles) and raw stages in the ring
+    static constexpr int NB = WMAX <= 32 ? 3 : 2;
+    static constexpr int P = WMAX <= 32 ? 4 : (WMAX <= 64 ? 4 : 3);
     static constexpr int BAR = 128;                                   // mbarriers, TMEM slot, job
     static constexpr int SMEM = NB * MMA_STAGE + P * RAW_STAGE + BAR;
     static_assert(SMEM * CTAS + 1024 * CTAS <= 233472, "shared memory plan too large");
@@ -346,6 +354,11 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
         const c64 *__restrict__ A = g.A[z] + J.a;
         const c64 *__restrict__ B = g.B[z] + J.b;
         const bool conjA = J.flags & GJ_CONJA, conjB = J.flags & GJ_CONJB;
+        // pre-split A: the job's blocks of this tile row, from this CTA's first k-step on
+        const bool pre = (J.flags & GJ_PRESPLIT) && g.ps[z] != nullptr;
+        const float *psrc = pre ? g.ps[z] + J.ps +
+                                      ((int64_t)(i0 / TC_BM) * ((J.k + TC_BK - 1) / TC_BK) + kbeg / TC_BK) * 4096
+                                : nullptr;
         // cp.async of one raw stage (k = l0 .. l0 + 7): 1024 A elements (4 per thread) and
         // w x 8 B elements, mapped so that consecutive threads read consecutive addresses
         const bool a_rows = (J.ars == 1), b_cols = (J.bcs == 1);
@@ -353,7 +366,7 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
             const int l0 = kbeg + TC_BK * st;
             const uint32_t ra = rbase + slot * PL::RAW_STAGE, rb = ra + PL::RAW_A;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 4 && !pre; ++q) {
                 const int e = tid + 256 * q;
                 const int row = a_rows ? (e & 127) : (e >> 3), l = a_rows ? (e >> 7) : (e & 7);
                 const bool v = (i0 + row < J.m) && (l0 + l < kend);
@@ -376,7 +389,7 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
             const unsigned char *ra = raw + slot * PL::RAW_STAGE;
             unsigned char *pa = smem + buf * PL::MMA_STAGE;
             c64 v[4];
-            {
+            if (!pre) {
                 const float4 h0 = *reinterpret_cast<const float4 *>(ra + 16 * tid);
                 const float4 h1 = *reinterpret_cast<const float4 *>(ra + 16 * (TC_BM * 2) + 16 * tid);
                 v[0] = mk<float>(h0.x, h0.y); v[1] = mk<float>(h0.z, h0.w);
@@ -412,6 +425,16 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
             cp_async_commit();
             const int buf = s % NB;
             if (s >= NB && ok && !mbar_wait(mempty + 8 * buf, ((s - NB) / NB) & 1)) ok = false;
+            if (pre && tid == 0 && ok) {            // the stage's A planes: one 16 KB bulk copy
+                asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(mfull + 8 * buf),
+                             "r"(4 * TC_PLANE_A)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        sbase + (uint32_t)(buf * PL::MMA_STAGE)),
+                    "l"(psrc + (int64_t)s * 4096), "r"(4 * TC_PLANE_A), "r"(mfull + 8 * buf)
+                    : "memory");
+            }
             convert(s % P, buf);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(mfull + 8 * buf);
@@ -419,6 +442,10 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
         cp_async_wait<0>();
         const int p = nst - 1;                      // its commit covers every earlier MMA
         if (ok && !mbar_wait(mempty + 8 * (p % NB), (p / NB) & 1)) ok = false;
+        // after a timeout, the last stages' bulk copies may still be in flight: wait for their
+        // stages to fill (bounded) before the CTA's shared memory is released
+        if (pre && tid == 0 && !ok)
+            for (int q = nst > NB ? nst - NB : 0; q < nst; ++q) mbar_wait(mfull + 8 * (q % NB), (q / NB) & 1);
         fence_after_sync();
     }
     ok = __syncthreads_and(ok);
@@ -475,6 +502,55 @@ __global__ void __launch_bounds__(TC_THREADS, TcPlan<WMAX>::CTAS) k_gemm_tc(Gemm
 
 }  // namespace
 
+// One 16 KB pre-split block per CTA: the 128 x 8 tile (rt, ks) of a PJob's operand, read
+// column by column (rows contiguous) into shared memory, then written as the four TF32 planes
+// in the canonical layout (each thread four consecutive floats: one row, four k), zero outside
+// the operand.  The split is the converters' (tf32_round), so both paths give the same planes.
+__global__ void __launch_bounds__(256) k_presplit(PresplitArgs g) {
+    const int z = blockIdx.z;
+    const int64_t blk = blockIdx.x;
+    const int tid = threadIdx.x;
+    __shared__ c64 tile[TC_BK][TC_BM];
+    __shared__ int s_job;
+    if (tid == 0) {
+        int lo = 0, hi = g.njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.jobs[mid].blk0 <= blk) lo = mid; else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const PJob J = g.jobs[s_job];
+    const int nks = (J.k + TC_BK - 1) / TC_BK;
+    const int64_t rel = blk - J.blk0;
+    const int rt = (int)(rel / nks), ks = (int)(rel % nks);
+    const c64 *__restrict__ A = (J.base ? g.finv[z] : g.pool[z]) + J.a;
+    for (int e = tid; e < TC_BM * TC_BK; e += 256) {
+        const int r = e & (TC_BM - 1), kk = e / TC_BM;
+        const int i = rt * TC_BM + r, l = ks * TC_BK + kk;
+        tile[kk][r] = (i < J.m && l < J.k) ? A[i + (int64_t)l * J.acs] : mk<float>(0.f, 0.f);
+    }
+    __syncthreads();
+    float *out = g.out[z] + J.ps + rel * 4096;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int f = 4 * (tid + 256 * q);        // four consecutive floats of the block
+        const int pl = f >> 10, w = f & 1023;     // plane, offset in the plane
+        const int cm = w >> 5;                    // core matrix: row group * 2 + k-group
+        const int row = (cm >> 1) * 8 + ((w & 31) >> 2), kk0 = (cm & 1) * 4;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const c64 x = tile[kk0 + e][row];
+            const float c = (pl < 2) ? x.re : x.im;
+            const float hi = tf32_round(c);
+            v[e] = (pl & 1) ? tf32_round(c - hi) : hi;
+        }
+        *reinterpret_cast<float4 *>(out + f) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 template <int WMAX> void launch_tc_w(const GemmArgs<float> &g, dim3 grid, cudaStream_t st) {
     static bool attr_set[64] = {};                  // per device: the kernel's shared-memory opt-in
     int dev = 0;
@@ -484,6 +560,12 @@ template <int WMAX> void launch_tc_w(const GemmArgs<float> &g, dim3 grid, cudaSt
         attr_set[dev] = true;
     }
     k_gemm_tc<WMAX><<<grid, TC_THREADS, TcPlan<WMAX>::SMEM, st>>>(g);
+}
+
+void launch_presplit(const PresplitArgs &g, int64_t nblocks, int ninst, cudaStream_t st) {
+    if (nblocks <= 0 || g.njobs <= 0) return;
+    k_presplit<<<dim3((unsigned)nblocks, 1, ninst), 256, 0, st>>>(g);
+    count_launch();
 }
 
 void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st) {

@@ -17,6 +17,7 @@ template <class T> struct GemmArgs {
     const cx<T> *A[MAX_INST];
     const cx<T> *B[MAX_INST];
     cx<T> *C[MAX_INST];
+    const float *ps[MAX_INST];           // pre-split A planes of GJ_PRESPLIT jobs, or null
 };
 
 template <class T> struct DiagArgs {
@@ -133,6 +134,16 @@ template <class T>
 void launch_gemm(const GemmArgs<T> &g, int ninst, cudaStream_t st, double flops = 0.0, double bytes = 0.0);
 // complex64 tcgen05 GEMM (tiles 128 x <= 128, bm = bn = 128 in the job tiling)
 void launch_gemm_tc(const GemmArgs<float> &g, dim3 grid, cudaStream_t st);
+// Build the pre-split tensor-core planes of every PJob (one 16 KB block per CTA, grid.z =
+// instances): instance z reads pool[z] / finv[z] and writes out[z].
+struct PresplitArgs {
+    const PJob *jobs;
+    int njobs;
+    const cx<float> *pool[MAX_INST];
+    const cx<float> *finv[MAX_INST];
+    float *out[MAX_INST];
+};
+void launch_presplit(const PresplitArgs &g, int64_t nblocks, int ninst, cudaStream_t st);
 // device status word of the tensor-core GEMM: 0, or ZOLO_ETIMEOUT after an expired
 // mbarrier wait (ZOLO_ECUDA when it cannot be read); `reset` clears a non-zero word
 int gemm_tc_status(bool reset);
