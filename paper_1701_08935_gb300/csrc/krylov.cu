@@ -748,13 +748,16 @@ static int gmres_block(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, 
 
 // The columns of X are independent GMRES problems: process them in chunks whose Krylov
 // basis, (m_max + 1) n x chunk complex128 blocks, fits a memory budget (100 GiB, or 60%
-// of the free device memory if that is smaller), and of at most opts.gmres_chunk columns.
+// of the free device memory plus the basis blocks this handle already holds, which are
+// reused, if that is smaller), and of at most opts.gmres_chunk columns.
 int gmres_apply(zolo_factor_s *h, int64_t k, const c128 *X, int64_t ldx, c128 *Y, int64_t ldy, cudaStream_t st,
                 zolo_stats *stats) {
     const int mmax = std::max(1, h->opts.gmres_m_max > 0 ? h->opts.gmres_m_max : 100);
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    const double budget = std::min(100.0 * (1ull << 30), 0.6 * (double)fr);
+    double held = 0.0;
+    for (const Buf &b : work(h).vblocks) held += (double)b.bytes;
+    const double budget = std::min(100.0 * (1ull << 30), 0.6 * ((double)fr + held));
     const double per_col = (double)(mmax + 1) * h->n * sizeof(c128);
     int64_t chunk = std::max<int64_t>(1, (int64_t)(budget / per_col));
     if (chunk >= 32) chunk = chunk / 32 * 32;
