@@ -36,7 +36,7 @@
 // that stage's "full" mbarrier.  A ninth warp issues each stage's six MMAs once it is full and
 // commits them to the stage's "empty" mbarrier, which the converters wait on before they
 // overwrite it, so the MMA issue never holds up the conversion.  The plan depends on the
-// widest tile of the launch (WMAX = 32, 64, 128: NB = 2 and P = 6, 4, 3), two CTAs per
+// widest tile of the launch (WMAX = 32, 64, 128: NB = 3, 2, 2 and P = 4, 4, 3), two CTAs per
 // SM; 128-wide tiles keep Cr and Ci in separate accumulators (twelve MMAs of N = w per
 // k-step) to fit.  Every wait on an mbarrier is bounded in time (2 s): on expiry the thread skips
 // its remaining waits, the CTA skips its epilogue, records ZOLO_ETIMEOUT in a device status
