@@ -463,7 +463,8 @@ def roofline(Z, prec, gp, stp, flops_alg, t_step_ms):
         # the DRAM / algorithmic ratio ncu measured on the same kernel's top-level solve products
         # of the 48^3 case of this recipe (89.4 MB read + written for 88.5 MB algorithmic)
         tc_launches = max(1, gp["tc_launches"])
-        roof.update({"kernel": "k_gemm_tc (tcgen05.mma kind::tf32, 3xTF32 complex64 front / solve products)",
+        roof.update({"kernel": "k_gemm_tc (tcgen05.mma kind::tf32, 3xTF32 complex64 front / solve products; "
+                               "solve operands pre-split into TF32 planes)",
                      "traffic": gp["tc_bytes"] / tc_launches * TC_DRAM_OVER_ALG,
                      "traffic_def": "bytes per launch: algorithmic bytes per launch x DRAM/algorithmic ratio "
                                     f"{TC_DRAM_OVER_ALG} measured by ncu on the 48^3 case (scaled by units)",

@@ -244,6 +244,10 @@ void zolo_symbolic_destroy(zolo_symbolic s);
 /* Upload the pencil and factor K_j = A - sigma_hat_j B, j = 1..r1, by the multifrontal
  * method on the device (the factorisation step of Algorithm 2): no-pivot LU of every front, level by
  * level, with the poles batched in each launch.  `sym` may be NULL (analysed here).
+ * Device memory per pole: the fronts (sum of nf^2 entries), their pivot-block inverses, and
+ * in ZOLO_PREC_MIXED a second copy of the large fronts' solve operands split into TF32
+ * planes for the tensor cores (16 bytes per entry, rebuilt by every factorisation; left
+ * out when it would take more than half of the free memory).
  * ESINGULAR on a zero / non-finite pivot.  Synchronises `stream`.               */
 int  zolo_factor(const zolo_csr *A, const zolo_csr *B, zolo_filter f, zolo_symbolic sym,
                  const zolo_opts *opts, void *stream, zolo_factor_h *out);
