@@ -7,6 +7,7 @@ fails.  A pin that still passed would not be tying the oracle to the paper."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle import apply as AP
 from oracle import eigs as E
@@ -240,3 +241,88 @@ def test_trapezoidal_nodes_without_the_half_step(monkeypatch):
             self.sigma_hat, self.w_hat = self.z[upper], -self.c[upper]
     monkeypatch.setattr(F, "ContourFilter", Wrong)
     assert _fails(T_FLT.test_citz_closed_form, 8)
+
+
+# ---------------------------------------------------------------- the inner operator G (eq. solve)
+def test_inner_operator_with_k_inverse_for_the_conjugate_pole(monkeypatch):
+    class Wrong(AP.InnerOperator):
+        def __call__(self, V):
+            BV = self.B @ V
+            out = self.flt.const_hat * V
+            for sol, w in zip(self.solvers, self.flt.w_hat):
+                out = out + w * sol.solve(BV) + np.conj(w) * sol.solve(BV)     # K^-1 in place of K^-H
+            return out
+    monkeypatch.setattr(AP, "InnerOperator", Wrong)
+    assert _fails(T_APPLY.test_three_definitions_agree, "real2d", (2, 2))
+
+
+# ---------------------------------------------------------------- Sylvester inertia
+def test_inertia_counting_positive_pivots(monkeypatch):
+    import scipy.linalg as sla
+
+    def wrong(A, B, sigma):
+        K = A.toarray() - sigma * B.toarray()
+        _, D, _ = sla.ldl(K, hermitian=True)
+        return int(np.sum(np.linalg.eigvalsh(D) > 0))
+    monkeypatch.setattr(E, "inertia_count", wrong)
+    assert _fails(T_EIGS.test_inertia_counts_match_dense)
+
+
+# ---------------------------------------------------------------- nested dissection (Section 2.3)
+def _nd_grid_variant(split_up=False, separator_first=False):
+    """oracle.ordering.nd_grid with one change: the split index rounded up, or the
+    separator numbered before its two halves."""
+    from oracle import ordering as O
+
+    def nd(dims, leaf_max=32):
+        dims = tuple(int(d) for d in dims) + (1,) * (3 - len(dims))
+        nx, ny, nz = dims
+        perm, first, npiv, parent = [], [], [], []
+        count = [0]
+
+        def emit(verts):
+            node = len(first)
+            first.append(count[0]); npiv.append(len(verts)); parent.append(-1)
+            perm.append(verts); count[0] += len(verts)
+            return node
+
+        def rec(box):
+            ext = [hi - lo for lo, hi in box]
+            if ext[0] * ext[1] * ext[2] == 0:
+                return None
+            if ext[0] * ext[1] * ext[2] <= leaf_max:
+                return emit(O._box_vertices(box, nx, ny))
+            ax = int(np.argmax(ext))
+            lo, hi = box[ax]
+            s = lo + (hi - lo + (1 if split_up else 0)) // 2
+            lower = list(box); lower[ax] = (lo, s)
+            upper = list(box); upper[ax] = (s + 1, hi)
+            sep = list(box); sep[ax] = (s, s + 1)
+            if separator_first:
+                node = emit(O._box_vertices(sep, nx, ny))
+                kids = [rec(lower), rec(upper)]
+            else:
+                kids = [rec(lower), rec(upper)]
+                node = emit(O._box_vertices(sep, nx, ny))
+            for k in kids:
+                if k is not None:
+                    parent[k] = node
+            return node
+
+        rec([(0, nx), (0, ny), (0, nz)])
+        return O.Tree(np.concatenate(perm), first, npiv, parent)
+    return nd
+
+
+def test_nested_dissection_variants_match_the_oracle_when_unchanged():
+    from oracle import ordering as O
+    a, b = _nd_grid_variant()((7, 5, 3), 4), O.nd_grid((7, 5, 3), 4)
+    assert np.array_equal(a.perm, b.perm) and np.array_equal(a.parent, b.parent)
+
+
+@pytest.mark.parametrize("change", ["split_up", "separator_first"])
+def test_nested_dissection_split_or_order_changed(monkeypatch, change):
+    from oracle import ordering as O
+    import test_oracle_ordering as T_ORD
+    monkeypatch.setattr(O, "nd_grid", _nd_grid_variant(**{change: True}))
+    assert _fails(T_ORD.test_hand_derived_4x3)
