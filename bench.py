@@ -468,7 +468,8 @@ def roofline(Z, prec, gp, stp, flops_alg, t_step_ms):
                     "peak_def": "of measured: bf16_tflops_sustained x 1.1/2.25 (nominal TF32/bf16) / 3 (3xTF32)"}
         # DRAM traffic per launch: the algorithmic bytes of an average launch of this step times
         # the DRAM / algorithmic ratio ncu measured on the same kernel's top-level solve products
-        # of the 48^3 case of this recipe (89.4 MB read + written for 88.5 MB algorithmic)
+        # of the 48^3 case of this recipe (~172 MB read + written for 88.5 MB algorithmic: the
+        # pre-split A planes are 16 bytes per element)
         tc_launches = max(1, gp["tc_launches"])
         roof.update({"kernel": "k_gemm_tc (tcgen05.mma kind::tf32, 3xTF32 complex64 front / solve products; "
                                "solve operands pre-split into TF32 planes)",
