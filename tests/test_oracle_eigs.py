@@ -153,3 +153,18 @@ def test_relerr_and_residual_complex_hand_values():
     lam = np.array([1.0])
     assert E.relerr(A, B, lam, X, -1.0, 0.5) == pytest.approx(1.0 / math.sqrt(5.0), rel=1e-14)
     assert E.residuals(A, B, lam, X)[0] == pytest.approx(1.0 / (3.0 * math.sqrt(2.0)), rel=1e-14)
+
+
+def test_lowest_eigenpairs_with_an_unbounded_left_gap():
+    """The mode of Section 3.1's Example 1: a- = -inf, a+ = lam_1, b- = lam_20, b+ = lam_21 on
+    the Gaussian-well Hamiltonian (8^3, B = I), r = (4, 4), one subspace iteration of 21
+    columns with exact poles: the 20 smallest eigenvalues of the dense eigensolver."""
+    p = synth.hamiltonian_wells(8, 2)
+    lam = np.linalg.eigvalsh(p.A.toarray())
+    flt = F.ZoloFilter(-math.inf, lam[0], lam[19], lam[20], 4, 4)
+    a, b = lam[0] - 0.5 * (lam[19] - lam[0]), 0.5 * (lam[19] + lam[20])
+    X0 = synth.random_block(p.n, 21, 3, complex_=False)
+    ev, X = E.subspace_iteration(p.A, p.B, a, b, X0, lambda Q: AP.apply_exact(p.A, p.B, Q, flt), n_iter=1)
+    assert len(ev) == 20
+    assert np.allclose(ev, lam[:20], rtol=1e-11, atol=0)
+    assert np.max(E.residuals(p.A, p.B, ev, X)) < 1e-9
